@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the all-longest-repeats (all-LR) query on GB300.
+
+One step = one lr_query_all over the whole n = 256 Mi English-like workload
+(Zipf(1.1) words over a 50k vocabulary, 96-symbol alphabet, seed 3), with
+rank and lcp resident in HBM: the Lemma 1 gather, the compaction, the
+covering-max sweep and the CSR writer, all in the library's CUDA kernels.
+The inputs (2 GiB) are larger than the 129 MB L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  Besides the device-resident throughput it
+reports: e2e (the same query through the host-buffer entry point, pinned
+host memory, H2D and D2H inside the timed region), the roofline of the
+dominant kernel and of the whole path against the measured HBM copy
+bandwidth, the CPU oracle timed on a bounded sample on the host cores, and
+the SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (Algorithm 3 of the paper) on the same
+workload, a bounded block of positions per step.
+
+With torchrun (N > 1) each rank runs an independent replica of the query on
+its own GPU (the query of one string does not shard); value is the positions
+of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "all-LR query Gpositions/s and % of HBM roofline at n=256M; serving p50/p99"
+UNIT = "Gpositions/s"
+WORKLOAD = "english_256m"
+
+
+# --------------------------------------------------------------------------- helpers
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1501_06663_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged since."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent or ent.get("workload") != workload:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def load_workload(name: str, n: int | None, ws: int, rank: int):
+    """Rank 0 generates and preps; other ranks load its arrays from a shared temp dir."""
+    import workloads as W
+    if ws == 1:
+        return W.single(name, n)
+    import torch.distributed as dist
+    tag = "lr_bench_%s_%s" % (name, n or "full")
+    d = os.path.join("/dev/shm" if os.path.isdir("/dev/shm") else tempfile.gettempdir(), tag)
+    if rank == 0:
+        w = W.single(name, n)
+        os.makedirs(d, exist_ok=True)
+        for k in ("text", "sa", "rank", "lcp"):
+            np.save(os.path.join(d, k + ".npy"), getattr(w, k))
+    dist.barrier()
+    if rank != 0:
+        arrs = {k: np.load(os.path.join(d, k + ".npy")) for k in ("text", "sa", "rank", "lcp")}
+        w = W.Workload(name, arrs["text"], arrs["sa"], arrs["rank"], arrs["lcp"])
+    dist.barrier()
+    if rank == 0:
+        import shutil
+        shutil.rmtree(d, ignore_errors=True)
+    return w
+
+
+def cpu_oracle_rate(w, target_s: float, seed: int = 0):
+    """Algorithm 3 (the oracle as it stands) over a contiguous block of positions."""
+    import oracle
+    n = w.n
+    rng = np.random.default_rng(seed)
+    probe = 20000
+    a = int(rng.integers(0, max(1, n - probe)))
+    t0 = time.perf_counter()
+    oracle.lr_at(w.rank, w.lcp, np.arange(a, min(n, a + probe)))
+    dt = max(time.perf_counter() - t0, 1e-4)
+    block = int(min(n, max(probe, probe * target_s / dt)))
+    a = int(rng.integers(0, max(1, n - block)))
+    ks = np.arange(a, a + block, dtype=np.int64)
+    t0 = time.perf_counter()
+    oracle.lr_at(w.rank, w.lcp, ks)
+    dt = time.perf_counter() - t0
+    return block / dt / 1e9, block, a, dt
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1501_06663_gb300 as lr
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lr.build_library() if rank == 0 else None
+    if ws > 1:
+        dist.barrier()
+    w = load_workload(args.workload, args.n, ws, rank)
+    n = w.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lr.lr_create(local)
+    d_rank = torch.from_numpy(w.rank).to(dev)
+    d_lcp = torch.from_numpy(w.lcp).to(dev)
+    ln = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    starts = torch.empty(1, dtype=torch.int32, device=dev)
+    status, total = lr.lr_query_all(ctx, d_rank, d_lcp, ln, st, off, starts, stream)
+    if status not in (lr.LR_OK, lr.LR_ERR_CAPACITY):
+        raise lr.LRError(status, "lr_query_all")
+    starts = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+
+    def step():
+        s, _ = lr.lr_query_all(ctx, d_rank, d_lcp, ln, st, off, starts, stream, sync=False)
+        if s != lr.LR_OK:
+            raise lr.LRError(s, "lr_query_all")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = lr.lr_last_launch_count(ctx) * args.steps
+    dstat = lr.lr_device_status(ctx, stream)
+    if dstat != lr.LR_OK:
+        raise lr.LRError(dstat, "device status after the timed steps")
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-kernel durations (CUDA events on the launching stream, recorded by the library)
+    lr.lr_set_phase_timing(ctx, True)
+    per = None
+    reps = max(3, min(args.steps, 20))
+    for _ in range(reps):
+        step()
+        t = lr.lr_phase_times(ctx)
+        per = [0.0] * len(t) if per is None else per
+        per = [a + b for a, b in zip(per, t)]
+    per = [p / reps for p in per]
+    lr.lr_set_phase_timing(ctx, False)
+
+    # e2e through the host-buffer entry point, pinned host memory
+    h_rank = torch.from_numpy(w.rank).pin_memory()
+    h_lcp = torch.from_numpy(w.lcp).pin_memory()
+    h_ln = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_st = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    h_starts = torch.empty(max(total, 1), dtype=torch.int32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    lr.lr_query_all_host(ctx, h_rank, h_lcp, h_ln, h_st, h_off, h_starts, stream)   # warm the buffers
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s, tot2 = lr.lr_query_all_host(ctx, h_rank, h_lcp, h_ln, h_st, h_off, h_starts, stream)
+        if s != lr.LR_OK or tot2 != total:
+            raise lr.LRError(s, "lr_query_all_host")
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    lr.lr_destroy(ctx)
+
+    if rank == 0:
+        import oracle
+        peak, peak_kind = measured_peaks()
+        cs, _ = oracle.compact(w.rank, w.lcp)
+        m = int(cs.size)
+        names = ["k_llr_compact", "k_cover"]
+        algo = {
+            # Lemma 1 inputs (rank, lcp) + the compact LLR array written
+            "k_llr_compact": 8.0 * n + 8.0 * m,
+            # compact LLR array read + lr_len, lr_start, offsets, starts written
+            "k_cover": 8.0 * m + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total,
+        }
+        dom = int(np.argmax(per))
+        kname = names[dom]
+        achieved = algo[kname] / (per[dom] * 1e-3) / 1e9
+        path_bytes = 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
+        path_achieved = path_bytes / (ms * 1e-3) / 1e9
+        value = ws * n / (ms * 1e-3) / 1e9
+        rate, block, a0, dt = cpu_oracle_rate(w, args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "parallelism": "replicas" if ws > 1 else "single",
+                       "inputs": "rank+lcp resident in HBM (%.2f GiB, larger than the 129 MB L2: no flush)"
+                                 % ((8 * n + 4) / 2**30),
+                       "total_lr_starts": total, "compact_llr": m},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": recorded_traffic(kname, args.workload),
+                         "algorithmic_bytes_per_launch": algo[kname], "avg_launch_ms": round(per[dom], 4)},
+            "path_roofline": {"bound": "hbm", "achieved": round(path_achieved, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(path_achieved / peak, 4), "peak_kind": peak_kind,
+                              "algorithmic_bytes_per_step": path_bytes},
+            "kernel_ms": {nm: round(p, 4) for nm, p in zip(names, per)},
+            "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
+                                       "[%d, %d) of the same workload, %.1f s single-threaded" % (a0, a0 + block, dt)},
+            "e2e": {"value": round(ws * n / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * n + 4 * (n + 1),
+                    "d2h_bytes_per_step": 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, local = dist_info()
+    if rank != 0:
+        return
+    import workloads as W
+    w = W.single(args.workload, args.n)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, 0.5, seed=1)
+    rates, blocks, secs = [], 0, 0.0
+    for k in range(args.steps):
+        rate, block, a0, dt = cpu_oracle_rate(w, args.ref_step_seconds, seed=100 + k)
+        blocks += block
+        secs += dt
+    value = blocks / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": w.n, "parallelism": "single"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "Algorithm 3 on %d random contiguous blocks, %d positions in total" % (args.steps, blocks)},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="shrink the workload (same seed); default full size")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

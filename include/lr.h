@@ -1,0 +1,144 @@
+/*
+ * lr.h -- C ABI of the GB300 longest-repeat query library (liblr.so).
+ *
+ * The library answers the longest repeat (LR) query of Tian and Xu, "On
+ * Longest Repeat Queries Using GPU" (arXiv 1501.06663), Sec. 2: for every
+ * position k of a string S[0..n), the longest substrings that cover k and
+ * occur at least twice in S (overlapping occurrences count), or the fact
+ * that none exists (S[k] is a singleton).  Several LR's may tie; the
+ * "all" calls list every one of them.
+ *
+ * Inputs are the arrays the paper builds on the host before the query and
+ * copies to the GPU (Sec. 4): the rank array and the lcp array of S, here
+ * 0-based:
+ *   rank[i] = r  iff  sa[r] = i                          (int32, n entries)
+ *   lcp[0] = lcp[n] = 0, lcp[r] = |lcp(S[sa[r-1]..], S[sa[r]..])| for 0<r<n
+ *                                                         (int32, n+1 entries)
+ * The string itself is not needed (Lemma 1 reads only rank and lcp).
+ *
+ * Outputs, per position k (0-based):
+ *   lr_len[k]    length of LR_k, 0 if none                          (int32)
+ *   lr_start[k]  start of the leftmost LR_k, -1 if none             (int32)
+ * and, for the "all" calls, a CSR list of every LR_k:
+ *   offsets[k] .. offsets[k+1]  the range of starts[] for position k (int64, n+1)
+ *   starts[j]    start positions, ascending within each k             (int32)
+ * so lr_start[k] == starts[offsets[k]] whenever lr_len[k] > 0.
+ *
+ * Conventions for every call:
+ *  - d_* pointers are device memory owned by the caller; h_* pointers are
+ *    host memory.  No pointer is retained after the call returns.
+ *  - Calls are asynchronous on `stream` (NULL = the legacy default stream)
+ *    unless they take an h_* output, which makes them wait for the stream.
+ *  - The library owns only its scratch (tile status words, the compact LLR
+ *    array), cached in the context and grown on demand; a context must not
+ *    be used from two host threads at once.
+ *  - No C++ exception crosses this interface.  Errors are returned as
+ *    lr_status.  Malformed device inputs (a rank outside [0, n), lcp[0] or
+ *    lcp[n] not 0) are detected by the kernels, never read out of bounds,
+ *    and reported through lr_device_status() (or by the synchronising calls).
+ */
+#ifndef LR_H_
+#define LR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LR_OK = 0,
+    LR_ERR_ARG = 1,        /* null pointer, n out of [1, 2^31 - 2], bad option  */
+    LR_ERR_SENTINEL = 2,   /* lcp[0] or lcp[n] is not 0, or a rank is out of range */
+    LR_ERR_CAPACITY = 3,   /* starts_capacity < total; *h_total holds the total   */
+    LR_ERR_NOMEM = 4,      /* a scratch allocation failed                          */
+    LR_ERR_CUDA = 5,       /* a CUDA runtime call failed; see lr_last_cuda_error   */
+    LR_ERR_TIMEOUT = 6,    /* a device-side wait gave up (results are invalid)    */
+    LR_ERR_BUSY = 7        /* the serving engine has no room for the job           */
+} lr_status;
+
+typedef struct lr_ctx lr_ctx;
+typedef struct CUstream_st* lr_stream_t;   /* same type as cudaStream_t */
+
+/* Create a context bound to CUDA device `device`.  *ctx is NULL on failure. */
+lr_status lr_create(lr_ctx** ctx, int device);
+/* Free the context and its scratch.  Waits for work the context queued. */
+lr_status lr_destroy(lr_ctx* ctx);
+/* Human-readable name of a status code (static string). */
+const char* lr_status_str(lr_status s);
+/* The last cudaError_t value seen by the context (0 if none). */
+lr_status lr_last_cuda_error(lr_ctx* ctx, int* code);
+
+/*
+ * Wait for `stream` and return the status the kernels of the context's
+ * previous asynchronous calls recorded (LR_OK, LR_ERR_SENTINEL or
+ * LR_ERR_TIMEOUT), then clear it.
+ */
+lr_status lr_device_status(lr_ctx* ctx, lr_stream_t stream);
+
+/*
+ * Leftmost LR of every position (Algorithm 2: compaction of the LLR array,
+ * Sec. 3.2, then for each k the longest compact LLR covering k, the leftmost
+ * on ties).  d_rank: n int32; d_lcp: n+1 int32; d_lr_start, d_lr_len: n
+ * int32 outputs.  Asynchronous.
+ */
+lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream,
+                            const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                            int32_t* d_lr_start, int32_t* d_lr_len);
+
+/*
+ * All LR's of every position (Algorithm 4 / Corollary 2: compaction, then
+ * the longest length per position and every compact LLR of that length that
+ * covers it), as the CSR described above.
+ *   d_offsets       n+1 int64 output; d_offsets[n] is the total
+ *   d_starts        output of starts_capacity int32 entries; entries past
+ *                   the capacity are not written
+ *   h_total         optional host output.  If non-NULL the call waits for
+ *                   `stream`, stores the total and returns LR_ERR_CAPACITY
+ *                   when it exceeds starts_capacity (lr_len, lr_start and
+ *                   offsets are still complete), or a device status.  If
+ *                   NULL the call is asynchronous; read d_offsets[n] and
+ *                   lr_device_status() later.
+ */
+lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream,
+                       const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                       int32_t* d_lr_len, int32_t* d_lr_start,
+                       int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
+                       int64_t* h_total);
+
+/*
+ * lr_query_all on host buffers: copies rank and lcp to device memory owned
+ * by the context, runs the query on `stream`, copies the results back and
+ * waits.  h_starts holds starts_capacity entries; *h_total receives the
+ * total, and LR_ERR_CAPACITY is returned if it does not fit (the other
+ * outputs are complete).  Host buffers may be pageable; pinned buffers copy
+ * faster.
+ */
+lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
+                            const int32_t* h_rank, const int32_t* h_lcp, int32_t n,
+                            int32_t* h_lr_len, int32_t* h_lr_start,
+                            int64_t* h_offsets, int32_t* h_starts, int64_t starts_capacity,
+                            int64_t* h_total);
+
+/*
+ * Kernels launched by the most recent query of this context (for the
+ * benchmark's launch accounting).
+ */
+int32_t lr_last_launch_count(lr_ctx* ctx);
+
+/*
+ * Per-kernel timing (instrumentation, off by default).  While enabled, each
+ * query records a CUDA event on its stream before and after every kernel it
+ * launches.  lr_phase_times() waits for the last query's events and writes
+ * the duration in milliseconds of each of its kernels, in launch order
+ * (k_llr_compact, k_cover), into ms[0 .. cap); it returns the number of
+ * kernels of that query, or -1 if timing was off or an event failed.
+ */
+lr_status lr_set_phase_timing(lr_ctx* ctx, int32_t enable);
+int32_t lr_phase_times(lr_ctx* ctx, float* ms, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LR_H_ */

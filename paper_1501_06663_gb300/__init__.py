@@ -1,0 +1,210 @@
+"""Python binding of liblr, the GB300 longest-repeat query library.
+
+Argument marshalling only: every step of the query runs in the CUDA kernels
+of ``liblr.so`` (sources in ``csrc/``, C ABI in ``include/lr.h``).  PyTorch
+supplies device memory and streams.  There is no CPU fallback: if the
+library is missing or cannot load, importing the functions below raises.
+
+The names follow the C ABI (``lr_create``, ``lr_query_all`` ...); ``Context``
+wraps a context handle with tensor-friendly methods that allocate outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import LIB_PATH, build_library  # noqa: F401
+
+_lib = None
+
+LR_OK = 0
+LR_ERR_ARG = 1
+LR_ERR_SENTINEL = 2
+LR_ERR_CAPACITY = 3
+LR_ERR_NOMEM = 4
+LR_ERR_CUDA = 5
+LR_ERR_TIMEOUT = 6
+LR_ERR_BUSY = 7
+
+#: every symbol include/lr.h declares
+EXPORTED = (
+    "lr_create", "lr_destroy", "lr_status_str", "lr_last_cuda_error", "lr_device_status",
+    "lr_query_leftmost", "lr_query_all", "lr_query_all_host", "lr_last_launch_count",
+    "lr_set_phase_timing", "lr_phase_times",
+)
+
+
+class LRError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s" % (what, status_str(status)))
+
+
+def load(path: str | None = None):
+    """Load liblr.so (raises OSError if it is missing: build it with build_library())."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("liblr.so not found at %s; run paper_1501_06663_gb300.build_library()" % p)
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, ci = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    lib.lr_create.argtypes = [ctypes.POINTER(vp), ci]
+    lib.lr_destroy.argtypes = [vp]
+    lib.lr_status_str.argtypes = [ci]
+    lib.lr_status_str.restype = ctypes.c_char_p
+    lib.lr_last_cuda_error.argtypes = [vp, ctypes.POINTER(ci)]
+    lib.lr_device_status.argtypes = [vp, vp]
+    lib.lr_query_leftmost.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    lib.lr_query_all.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_query_all_host.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_last_launch_count.argtypes = [vp]
+    lib.lr_last_launch_count.restype = i32
+    lib.lr_set_phase_timing.argtypes = [vp, i32]
+    lib.lr_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+    lib.lr_phase_times.restype = i32
+    for name in EXPORTED:
+        f = getattr(lib, name)
+        if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
+            f.restype = ci
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_str(status: int) -> str:
+    return load().lr_status_str(int(status)).decode()
+
+
+def _check(status: int, what: str, ok=(LR_OK,)):
+    if status not in ok:
+        raise LRError(status, what)
+    return status
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    """Device (or host) address of a tensor / numpy array, or NULL."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def lr_create(device: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lr_create(ctypes.byref(h), int(device)), "lr_create")
+    return h
+
+
+def lr_destroy(ctx) -> None:
+    _check(load().lr_destroy(ctx), "lr_destroy")
+
+
+def lr_device_status(ctx, stream=None) -> int:
+    return load().lr_device_status(ctx, _stream(stream))
+
+
+def lr_last_cuda_error(ctx) -> int:
+    code = ctypes.c_int()
+    _check(load().lr_last_cuda_error(ctx, ctypes.byref(code)), "lr_last_cuda_error")
+    return code.value
+
+
+def lr_last_launch_count(ctx) -> int:
+    return int(load().lr_last_launch_count(ctx))
+
+
+def lr_set_phase_timing(ctx, enable: bool) -> None:
+    _check(load().lr_set_phase_timing(ctx, 1 if enable else 0), "lr_set_phase_timing")
+
+
+def lr_phase_times(ctx, cap: int = 8):
+    """Milliseconds of each kernel of the last query (launch order), or None."""
+    buf = (ctypes.c_float * cap)()
+    k = load().lr_phase_times(ctx, buf, cap)
+    return None if k < 0 else [float(buf[i]) for i in range(min(k, cap))]
+
+
+def lr_query_leftmost(ctx, rank, lcp, lr_start, lr_len, stream=None) -> int:
+    n = int(rank.numel())
+    return load().lr_query_leftmost(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n,
+                                    _ptr(lr_start), _ptr(lr_len))
+
+
+def lr_query_all(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
+    """Returns (status, total or None)."""
+    n = int(rank.numel())
+    cap = int(starts.numel()) if starts is not None else 0
+    tot = ctypes.c_int64(-1)
+    st = load().lr_query_all(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len), _ptr(lr_start),
+                             _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot) if sync else None)
+    return st, (tot.value if sync else None)
+
+
+def lr_query_all_host(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None):
+    """Host (numpy or CPU tensor) buffers.  Returns (status, total)."""
+    n = int(rank.size if hasattr(rank, "size") and not callable(rank.size) else rank.numel())
+    cap = int(len(starts)) if starts is not None else 0
+    tot = ctypes.c_int64(-1)
+    st = load().lr_query_all_host(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len),
+                                  _ptr(lr_start), _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot))
+    return st, tot.value
+
+
+# ---------------------------------------------------------------- convenience
+
+class Context:
+    """A liblr context on one CUDA device, with output-allocating query methods."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.device = torch.device("cuda", device)
+        self.handle = lr_create(device)
+
+    def close(self):
+        if self.handle is not None:
+            lr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query_leftmost(self, rank, lcp, stream=None):
+        import torch
+        n = int(rank.numel())
+        lr_start = torch.empty(n, dtype=torch.int32, device=rank.device)
+        lr_len = torch.empty(n, dtype=torch.int32, device=rank.device)
+        _check(lr_query_leftmost(self.handle, rank, lcp, lr_start, lr_len, stream), "lr_query_leftmost")
+        _check(lr_device_status(self.handle, stream), "lr_query_leftmost (device)")
+        return lr_start, lr_len
+
+    def query_all(self, rank, lcp, capacity: int | None = None, stream=None):
+        """All LR's as CSR: (lr_len, lr_start, offsets, starts[:total])."""
+        import torch
+        n = int(rank.numel())
+        dev = rank.device
+        lr_len = torch.empty(n, dtype=torch.int32, device=dev)
+        lr_start = torch.empty(n, dtype=torch.int32, device=dev)
+        offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        cap = 2 * n + 1024 if capacity is None else int(capacity)
+        starts = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        st, total = lr_query_all(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+        if st == LR_ERR_CAPACITY:
+            starts = torch.empty(total, dtype=torch.int32, device=dev)
+            st, total = lr_query_all(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+        _check(st, "lr_query_all")
+        return lr_len, lr_start, offsets, starts[:total]

@@ -1,0 +1,322 @@
+// C ABI of liblr (declared in include/lr.h): contexts, argument checks,
+// scratch management and the host-buffer entry point.  All arithmetic of
+// the query runs in the kernels of lr_query.cu.
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdlib>
+#include <new>
+#include "lr.h"
+#include "lr_internal.h"
+#include "lr_device.cuh"
+
+struct lr_ctx {
+    int device = 0;
+    int last_cuda_error = 0;
+    int last_launches = 0;
+    unsigned* d_err = nullptr;            // sticky device error bits
+    unsigned char* scratch = nullptr;     // TileScratch storage
+    size_t scratch_bytes = 0;
+    long long scratch_n = 0;              // positions the scratch is laid out for
+    long long* h_pinned = nullptr;        // [0] total, [1] error bits
+    unsigned char* hostpath = nullptr;    // device buffers of lr_query_all_host
+    size_t hostpath_bytes = 0;
+    lr::PhaseEvents events;               // per-kernel timing (off by default)
+    bool events_created = false;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr long long kMaxN = 2147483646LL;  // lcp needs n+1 int32 entries
+
+// Makes ctx->device current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+lr_status cuda_fail(lr_ctx* ctx, cudaError_t e) {
+    ctx->last_cuda_error = (int)e;
+    return e == cudaErrorMemoryAllocation ? LR_ERR_NOMEM : LR_ERR_CUDA;
+}
+
+struct Layout {
+    size_t off_status_c, off_status_o, zero_end, off_cbase, off_cstart, off_cend, total;
+};
+
+Layout layout_for(long long n) {
+    const long long nt = lr::num_tiles(n);
+    Layout L;
+    L.off_status_c = kAlign;                       // tickets in [0, 8), per-query error bits at 16
+    L.off_status_o = align_up(L.off_status_c + (size_t)nt * 8);
+    L.zero_end = L.off_status_o + (size_t)nt * 8;
+    L.off_cbase = align_up(L.zero_end);
+    L.off_cstart = align_up(L.off_cbase + (size_t)(nt + 1) * 4);
+    L.off_cend = align_up(L.off_cstart + (size_t)n * 4);
+    L.total = align_up(L.off_cend + (size_t)n * 4);
+    return L;
+}
+
+// Grows the scratch to hold a query of n positions and fills `s`.
+lr_status get_scratch(lr_ctx* ctx, long long n, lr::TileScratch* s) {
+    if (n > ctx->scratch_n) {
+        const Layout L = layout_for(n);
+        if (ctx->scratch) {
+            cudaError_t e = cudaDeviceSynchronize();   // previous queries may still read it
+            if (e != cudaSuccess) return cuda_fail(ctx, e);
+            cudaFree(ctx->scratch);
+            ctx->scratch = nullptr; ctx->scratch_n = 0; ctx->scratch_bytes = 0;
+        }
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, L.total);
+        if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(ctx, e); }
+        ctx->scratch = (unsigned char*)p;
+        ctx->scratch_bytes = L.total;
+        ctx->scratch_n = n;
+    }
+    const Layout L = layout_for(ctx->scratch_n);
+    const long long nt = lr::num_tiles(n);
+    unsigned char* b = ctx->scratch;
+    s->tickets = (unsigned*)b;
+    s->qerr = (unsigned*)(b + 16);
+    s->err = ctx->d_err;
+    s->status_c = (unsigned long long*)(b + L.off_status_c);
+    s->status_o = (unsigned long long*)(b + L.off_status_o);
+    s->cbase = (int32_t*)(b + L.off_cbase);
+    s->cstart = (int32_t*)(b + L.off_cstart);
+    s->cend = (int32_t*)(b + L.off_cend);
+    s->ntiles = nt;
+    s->zero_base = b;
+    s->zero_bytes = L.off_status_o + (size_t)nt * 8;
+    return LR_OK;
+}
+
+lr_status check_n(int32_t n) {
+    return (n >= 1 && (long long)n <= kMaxN) ? LR_OK : LR_ERR_ARG;
+}
+
+lr_status device_bits_to_status(unsigned bits) {
+    if (bits & lr::kErrTimeout) return LR_ERR_TIMEOUT;
+    if (bits & lr::kErrInput) return LR_ERR_SENTINEL;
+    return LR_OK;
+}
+
+// Copies the total (offsets[n]) and the error bits to the host, waits, and
+// clears the error word.
+lr_status sync_total(lr_ctx* ctx, cudaStream_t stream, const int64_t* d_total, int64_t* h_total) {
+    cudaError_t e = cudaSuccess;
+    if (d_total) e = cudaMemcpyAsync(&ctx->h_pinned[0], d_total, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctx->h_pinned[1], ctx->d_err, 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_err, 0, 4, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if (h_total && d_total) *h_total = ctx->h_pinned[0];
+    return device_bits_to_status((unsigned)(ctx->h_pinned[1] & 0xffffffffu));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lr_status_str(lr_status s) {
+    switch (s) {
+        case LR_OK: return "LR_OK";
+        case LR_ERR_ARG: return "LR_ERR_ARG";
+        case LR_ERR_SENTINEL: return "LR_ERR_SENTINEL";
+        case LR_ERR_CAPACITY: return "LR_ERR_CAPACITY";
+        case LR_ERR_NOMEM: return "LR_ERR_NOMEM";
+        case LR_ERR_CUDA: return "LR_ERR_CUDA";
+        case LR_ERR_TIMEOUT: return "LR_ERR_TIMEOUT";
+        case LR_ERR_BUSY: return "LR_ERR_BUSY";
+    }
+    return "LR_ERR_UNKNOWN";
+}
+
+lr_status lr_create(lr_ctx** out, int device) {
+    if (!out) return LR_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return device < 0 ? LR_ERR_ARG : LR_ERR_CUDA;
+    }
+    lr_ctx* ctx = new (std::nothrow) lr_ctx();
+    if (!ctx) return LR_ERR_NOMEM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaError_t e = g.ok ? cudaSuccess : cudaErrorInvalidDevice;
+    if (e == cudaSuccess) e = lr::configure_kernels();
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_pinned, 64);
+    if (e != cudaSuccess) {
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? LR_ERR_NOMEM : LR_ERR_CUDA;
+    }
+    *out = ctx;
+    return LR_OK;
+}
+
+lr_status lr_destroy(lr_ctx* ctx) {
+    if (!ctx) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->hostpath) cudaFree(ctx->hostpath);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->events_created)
+        for (int i = 0; i <= lr::kMaxPhases; ++i) cudaEventDestroy(ctx->events.ev[i]);
+    delete ctx;
+    return LR_OK;
+}
+
+lr_status lr_last_cuda_error(lr_ctx* ctx, int* code) {
+    if (!ctx || !code) return LR_ERR_ARG;
+    *code = ctx->last_cuda_error;
+    return LR_OK;
+}
+
+int32_t lr_last_launch_count(lr_ctx* ctx) { return ctx ? ctx->last_launches : -1; }
+
+lr_status lr_set_phase_timing(lr_ctx* ctx, int32_t enable) {
+    if (!ctx) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    if (enable && !ctx->events_created) {
+        for (int i = 0; i <= lr::kMaxPhases; ++i) {
+            cudaError_t e = cudaEventCreate(&ctx->events.ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->events.ev[j]);
+                return cuda_fail(ctx, e);
+            }
+        }
+        ctx->events_created = true;
+    }
+    ctx->events.enabled = enable != 0;
+    return LR_OK;
+}
+
+int32_t lr_phase_times(lr_ctx* ctx, float* ms, int32_t cap) {
+    if (!ctx || !ctx->events.enabled || ctx->last_launches <= 0) return -1;
+    DeviceGuard g(ctx->device);
+    const int nk = ctx->last_launches;
+    if (cudaEventSynchronize(ctx->events.ev[nk]) != cudaSuccess) return -1;
+    for (int i = 0; i < nk && i < cap; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ctx->events.ev[i], ctx->events.ev[i + 1]) != cudaSuccess) return -1;
+        ms[i] = t;
+    }
+    return nk;
+}
+
+lr_status lr_device_status(lr_ctx* ctx, lr_stream_t stream) {
+    if (!ctx) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    return sync_total(ctx, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp,
+                            int32_t n, int32_t* d_lr_start, int32_t* d_lr_len) {
+    if (!ctx || !d_rank || !d_lcp || !d_lr_start || !d_lr_len) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr::TileScratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    cudaError_t e = lr::launch_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
+                                     (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
+    return e == cudaSuccess ? LR_OK : cuda_fail(ctx, e);
+}
+
+lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                       int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
+                       int64_t starts_capacity, int64_t* h_total) {
+    if (!ctx || !d_rank || !d_lcp || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
+    if (starts_capacity < 0 || (starts_capacity > 0 && !d_starts)) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr::TileScratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    cudaError_t e = lr::launch_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
+                                     starts_capacity, true, (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if (!h_total) return LR_OK;
+    st = sync_total(ctx, (cudaStream_t)stream, d_offsets + n, h_total);
+    if (st != LR_OK) return st;
+    return (*h_total > starts_capacity) ? LR_ERR_CAPACITY : LR_OK;
+}
+
+lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_rank, const int32_t* h_lcp,
+                            int32_t n, int32_t* h_lr_len, int32_t* h_lr_start, int64_t* h_offsets,
+                            int32_t* h_starts, int64_t starts_capacity, int64_t* h_total) {
+    if (!ctx || !h_rank || !h_lcp || !h_lr_len || !h_lr_start || !h_offsets || !h_total) return LR_ERR_ARG;
+    if (starts_capacity < 0 || (starts_capacity > 0 && !h_starts)) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    const size_t nn = (size_t)n;
+    const size_t o_rank = 0, o_lcp = align_up(o_rank + nn * 4), o_len = align_up(o_lcp + (nn + 1) * 4),
+                 o_start = align_up(o_len + nn * 4), o_off = align_up(o_start + nn * 4),
+                 o_starts = align_up(o_off + (nn + 1) * 8),
+                 need = align_up(o_starts + (size_t)starts_capacity * 4);
+    cudaStream_t strm = (cudaStream_t)stream;
+    cudaError_t e;
+    if (need > ctx->hostpath_bytes) {
+        if (ctx->hostpath) {
+            e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return cuda_fail(ctx, e);
+            cudaFree(ctx->hostpath);
+            ctx->hostpath = nullptr; ctx->hostpath_bytes = 0;
+        }
+        e = cudaMalloc((void**)&ctx->hostpath, need);
+        if (e != cudaSuccess) { cudaGetLastError(); return cuda_fail(ctx, e); }
+        ctx->hostpath_bytes = need;
+    }
+    unsigned char* b = ctx->hostpath;
+    int32_t* d_rank = (int32_t*)(b + o_rank);
+    int32_t* d_lcp = (int32_t*)(b + o_lcp);
+    int32_t* d_len = (int32_t*)(b + o_len);
+    int32_t* d_start = (int32_t*)(b + o_start);
+    int64_t* d_off = (int64_t*)(b + o_off);
+    int32_t* d_starts = (int32_t*)(b + o_starts);
+    e = cudaMemcpyAsync(d_rank, h_rank, nn * 4, cudaMemcpyHostToDevice, strm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_lcp, h_lcp, (nn + 1) * 4, cudaMemcpyHostToDevice, strm);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    lr::TileScratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    e = lr::launch_query(d_rank, d_lcp, n, s, d_len, d_start, d_off, d_starts, starts_capacity, true, strm,
+                         &ctx->last_launches, &ctx->events);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_lr_len, d_len, nn * 4, cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_lr_start, d_start, nn * 4, cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_offsets, d_off, (nn + 1) * 8, cudaMemcpyDeviceToHost, strm);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    st = sync_total(ctx, strm, d_off + n, h_total);
+    if (st != LR_OK) return st;
+    const int64_t tot = *h_total;
+    const int64_t copy = tot < starts_capacity ? tot : starts_capacity;
+    if (copy > 0) {
+        e = cudaMemcpyAsync(h_starts, d_starts, (size_t)copy * 4, cudaMemcpyDeviceToHost, strm);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+    }
+    return tot > starts_capacity ? LR_ERR_CAPACITY : LR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Device helpers shared by the longest-repeat kernels: acquire/release
+// accesses of tile status words and the warp-cooperative decoupled look-back
+// of a single-pass prefix scan (Merrill and Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", NVIDIA TR 2016), written for this
+// library.
+#pragma once
+#include <cstdint>
+
+namespace lr {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Error bits the kernels OR into the context's device error word.
+constexpr unsigned kErrInput = 1u;     // rank out of [0, n), lcp[0] / lcp[n] not 0, or an lcp too long
+constexpr unsigned kErrTimeout = 2u;   // a bounded wait on another tile gave up
+
+// A status word holds a 2-bit flag and a 62-bit value.
+constexpr unsigned long long kFlagShift = 62;
+constexpr unsigned long long kValMask = (1ull << kFlagShift) - 1;
+constexpr unsigned long long kAggregate = 1ull;   // value = this tile's own total
+constexpr unsigned long long kPrefix = 2ull;      // value = total of tiles 0..this one
+
+// Upper bound on polls of one status word before a wait is declared lost
+// (about a second at the back-off below).
+constexpr int kSpinLimit = 1 << 23;
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & (kWarp - 1); }
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        int y = __shfl_up_sync(kFull, v, o);
+        if (lane >= (unsigned)o) v += y;
+    }
+    return v;
+}
+
+// Called by one whole warp of the tile.  Publishes `aggregate` for `tile`,
+// sums the totals of all earlier tiles by looking back over their status
+// words, publishes the inclusive prefix and returns the exclusive one (the
+// same value in every lane).  Waits only on earlier tiles, which were
+// scheduled before this one, and gives up (setting kErrTimeout in *err and
+// *qerr) after kSpinLimit polls of any one word.
+__device__ inline long long lookback_exclusive(unsigned long long* status, long long tile,
+                                               long long aggregate, unsigned* err, unsigned* qerr) {
+    const unsigned lane = lane_id();
+    if (tile == 0) {
+        if (lane == 0) st_release(&status[0], (kPrefix << kFlagShift) | (unsigned long long)aggregate);
+        return 0;
+    }
+    if (lane == 0) st_release(&status[tile], (kAggregate << kFlagShift) | (unsigned long long)aggregate);
+    long long exclusive = 0;
+    long long base = tile - 1;
+    while (true) {
+        const long long t = base - (long long)lane;
+        unsigned long long w = (kPrefix << kFlagShift);   // before tile 0: prefix 0
+        if (t >= 0) {
+            int polls = 0;
+            w = ld_acquire(&status[t]);
+            while ((w >> kFlagShift) == 0) {
+                if (++polls >= kSpinLimit) {
+                    atomicOr(err, kErrTimeout);
+                    atomicOr(qerr, kErrTimeout);
+                    w = (kPrefix << kFlagShift);
+                    break;
+                }
+                __nanosleep(64);
+                w = ld_acquire(&status[t]);
+            }
+        }
+        const unsigned pmask = __ballot_sync(kFull, (w >> kFlagShift) == kPrefix);
+        const int stop = pmask ? __ffs(pmask) - 1 : kWarp - 1;
+        const long long contrib = ((int)lane <= stop) ? (long long)(w & kValMask) : 0;
+        exclusive += warp_sum_ll(contrib);
+        if (pmask) break;
+        base -= kWarp;
+    }
+    if (lane == 0) st_release(&status[tile], (kPrefix << kFlagShift) | (unsigned long long)(exclusive + aggregate));
+    return exclusive;
+}
+
+}  // namespace lr

@@ -1,0 +1,252 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer and index work: every comparison is bit-exact.  Small inputs are
+compared in full; the full-size workloads are compared on sampled positions
+(Algorithm 3 per position) plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = None
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    global P
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1501_06663_gb300 as lrmod
+    lrmod.build_library()
+    P = lrmod
+    c = lrmod.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu_all(ctx, rank, lcp):
+    out = ctx.query_all(_dev(rank), _dev(lcp))
+    return tuple(t.cpu().numpy() for t in out)
+
+
+def _assert_csr_equal(got, want, what=""):
+    names = ("lr_len", "lr_start", "offsets", "starts")
+    for name, a, b in zip(names, got, want):
+        assert a.shape == b.shape, (what, name, a.shape, b.shape)
+        if not np.array_equal(a, b):
+            bad = np.nonzero(a != b)[0][:10]
+            raise AssertionError("%s %s differs at %s: got %s want %s" % (what, name, bad, a[bad], b[bad]))
+
+
+def _full_check(ctx, text):
+    sa, rank, lcp = W.prep(text)
+    want = oracle.lr_all_raw(rank, lcp)
+    got = _gpu_all(ctx, rank, lcp)
+    _assert_csr_equal(got, want, "n=%d" % text.size)
+    st, ln = ctx.query_leftmost(_dev(rank), _dev(lcp))
+    assert np.array_equal(st.cpu().numpy(), want[1]) and np.array_equal(ln.cpu().numpy(), want[0])
+
+
+def _sampled_check(ctx, w, got, nsamples, seed):
+    """Sampled positions against Algorithm 3, plus size-independent properties."""
+    ln, st, off, starts = got
+    n = w.n
+    rng = np.random.default_rng(seed)
+    ks = np.unique(np.concatenate([rng.integers(0, n, nsamples), [0, 1, n - 2, n - 1],
+                                   np.arange(2040, 2060), np.arange(n - 2100, n - 2000)]))
+    ks = ks[(ks >= 0) & (ks < n)]
+    wl, ws, wo, wst = oracle.lr_at(w.rank, w.lcp, ks)
+    for q, k in enumerate(ks):
+        assert ln[k] == wl[q] and st[k] == ws[q], (k, ln[k], wl[q], st[k], ws[q])
+        assert np.array_equal(starts[off[k]:off[k + 1]], wst[wo[q]:wo[q + 1]]), k
+    # properties at every position
+    assert off[0] == 0 and off[n] == starts.size and np.all(np.diff(off) >= 0)
+    cnt = np.diff(off)
+    assert np.array_equal(cnt == 0, ln == 0) and np.all(st[ln == 0] == -1)
+    has = ln > 0
+    assert np.array_equal(st[has], starts[off[:-1][has]])
+    counts = np.bincount(w.text, minlength=256)
+    assert np.array_equal(ln == 0, counts[w.text] == 1)         # Lemma 1: none iff singleton
+
+
+# ------------------------------------------------------------------ small inputs
+
+def test_paper_examples(ctx):
+    for s in (b"mississippi", b"abcabcddbca", b"ababab", b"aaaa", b"a", b"ab", b"abcd", b"aa"):
+        _full_check(ctx, np.frombuffer(s, np.uint8))
+
+
+def test_random_small_strings(ctx):
+    import tests.test_oracle as T
+    rng = np.random.default_rng(99)
+    for trial in range(150):
+        n = int(rng.integers(1, 300)) if trial < 100 else int(rng.integers(300, 6000))
+        _full_check(ctx, np.frombuffer(T._random_string(rng, n), np.uint8))
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 2047, 2048, 2049, 4095, 4096, 4097, 6143, 10240, 65536 + 7])
+def test_tile_boundaries(ctx, n):
+    for kind, seed in (("dna_iid", 5), ("dna", 6), ("english", 7), ("protein", 8)):
+        _full_check(ctx, W.make_text(kind, n, seed))
+
+
+def test_degenerate_strings(ctx):
+    _full_check(ctx, np.full(5000, ord("a"), np.uint8))                  # one symbol
+    _full_check(ctx, np.arange(256, dtype=np.uint8))                       # all singletons
+    _full_check(ctx, np.frombuffer(b"ab" * 3000, np.uint8))                # period 2
+    _full_check(ctx, np.frombuffer((b"abcdefghij" * 700)[:6999], np.uint8))
+
+
+def test_long_repeats_cross_many_tiles(ctx):
+    rng = np.random.default_rng(3)
+    base = rng.integers(65, 69, 200_000).astype(np.uint8)
+    base[150_000:190_000] = base[10_000:50_000]                              # a 40k copy
+    base[100_000:100_300] = base[60_000:60_300]
+    _full_check(ctx, base)
+
+
+def test_wide_windows_spill_to_global(ctx):
+    """beta(k) > the shared-memory window: W candidates of equal length cover one position."""
+    rng = np.random.default_rng(4)
+    Wn = 4400
+    R = rng.integers(65, 69, 2 * Wn + 2).astype(np.uint8)
+    parts = [R]
+    for j in range(Wn):
+        parts.append(R[j:j + Wn + 1])
+        parts.append(np.array([ord("#")], np.uint8))
+    text = np.concatenate(parts)
+    w = W.Workload("wide", text, *W.prep(text))
+    got = _gpu_all(ctx, w.rank, w.lcp)
+    _sampled_check(ctx, w, got, 3000, 5)
+    ks = np.arange(Wn - 50, Wn + 50)
+    wl, ws, wo, wst = oracle.lr_at(w.rank, w.lcp, ks)
+    assert int(np.diff(wo).max()) >= 1
+    for q, k in enumerate(ks):
+        assert np.array_equal(got[3][got[2][k]:got[2][k + 1]], wst[wo[q]:wo[q + 1]])
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_dna_iid_1m_full(ctx):
+    w = W.single("dna_iid_1m")
+    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+
+
+def test_dna_planted_4m_full(ctx):
+    w = W.single("dna_64m", n=4 * W.MI)
+    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+
+
+def test_english_4m_full(ctx):
+    w = W.single("english_256m", n=4 * W.MI)
+    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+
+
+@pytest.mark.parametrize("name", ["dna_64m", "english_256m"])
+def test_full_size_sampled(ctx, name):
+    w = W.single(name)
+    got = _gpu_all(ctx, w.rank, w.lcp)
+    _sampled_check(ctx, w, got, 4000, 17)
+
+
+# ------------------------------------------------------------------ API behaviour
+
+def test_capacity_error_keeps_offsets(ctx):
+    w = W.single("dna_64m", n=100_000)
+    want = oracle.lr_all_raw(w.rank, w.lcp)
+    rank, lcp = _dev(w.rank), _dev(w.lcp)
+    n = w.n
+    ln = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    small = torch.full((1000,), -7, dtype=torch.int32, device="cuda")
+    status, total = P.lr_query_all(ctx.handle, rank, lcp, ln, st, off, small)
+    assert status == P.LR_ERR_CAPACITY and total == want[3].size
+    assert np.array_equal(off.cpu().numpy(), want[2]) and np.array_equal(ln.cpu().numpy(), want[0])
+    assert np.array_equal(small.cpu().numpy(), want[3][:1000])
+
+
+def test_host_buffer_entry_point(ctx):
+    w = W.single("english_256m", n=300_000)
+    want = oracle.lr_all_raw(w.rank, w.lcp)
+    n = w.n
+    ln = np.empty(n, np.int32)
+    st = np.empty(n, np.int32)
+    off = np.empty(n + 1, np.int64)
+    starts = np.empty(2 * n, np.int32)
+    status, total = P.lr_query_all_host(ctx.handle, w.rank, w.lcp, ln, st, off, starts)
+    assert status == P.LR_OK
+    _assert_csr_equal((ln, st, off, starts[:total]), want, "host")
+
+
+def test_invalid_arguments(ctx):
+    t = torch.zeros(4, dtype=torch.int32, device="cuda")
+    lib = P.load()
+    import ctypes
+    null = ctypes.c_void_p(0)
+    tot = ctypes.c_int64()
+    s = P._stream(None)
+    for n in (0, -5, 2**31 - 1):
+        assert lib.lr_query_all(ctx.handle, s, P._ptr(t), P._ptr(t), n, P._ptr(t), P._ptr(t), P._ptr(t),
+                                P._ptr(t), 4, ctypes.byref(tot)) == P.LR_ERR_ARG
+    assert lib.lr_query_all(ctx.handle, s, null, P._ptr(t), 3, P._ptr(t), P._ptr(t), P._ptr(t),
+                            P._ptr(t), 4, ctypes.byref(tot)) == P.LR_ERR_ARG
+    assert lib.lr_query_leftmost(ctx.handle, s, P._ptr(t), null, 3, P._ptr(t), P._ptr(t)) == P.LR_ERR_ARG
+
+
+def test_bad_sentinel_and_rank_are_reported(ctx):
+    w = W.single("dna_iid_1m", n=5000)
+    lcp = w.lcp.copy()
+    lcp[0] = 3
+    with pytest.raises(P.LRError) as e:
+        ctx.query_all(_dev(w.rank), _dev(lcp))
+    assert e.value.status == P.LR_ERR_SENTINEL
+    rank = w.rank.copy()
+    rank[17] = w.n + 100                                                   # out of range: clamped, reported
+    with pytest.raises(P.LRError) as e:
+        ctx.query_all(_dev(rank), _dev(w.lcp))
+    assert e.value.status == P.LR_ERR_SENTINEL
+    # the context stays usable
+    got = _gpu_all(ctx, w.rank, w.lcp)
+    _assert_csr_equal(got, oracle.lr_all_raw(w.rank, w.lcp))
+
+
+def test_maximum_size_closed_form(ctx):
+    """S = a^n with n = 2^31 - 2, the largest n the ABI takes.
+
+    sa[r] = n-1-r, rank[i] = n-1-i, lcp = [0, 1, ..., n-1, 0]; so L_0 = n-1,
+    L_i = n-i, only <0, n-1> and <1, n-1> are useful, and LR_k is {0} for
+    k = 0, {0, 1} for 0 < k < n-1 and {1} for k = n-1, all of length n-1.
+    The total (2n - 2) exceeds 2^31, exercising the int64 offsets.
+    """
+    free, _ = torch.cuda.mem_get_info()
+    n = 2**31 - 2
+    need = n * (4 + 4 + 4 + 4 + 8 + 8 + 8) + (1 << 30)
+    if free < need:
+        pytest.skip("needs %.0f GB free" % (need / 1e9))
+    rank = torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda")
+    lcp = torch.arange(0, n + 1, dtype=torch.int32, device="cuda")
+    lcp[n] = 0
+    ln, st, off, starts = ctx.query_all(rank, lcp, capacity=2 * n)
+    del rank, lcp
+    assert int(off[n]) == 2 * n - 2
+    assert bool((ln == n - 1).all())
+    assert bool((st[:n - 1] == 0).all()) and int(st[n - 1]) == 1
+    step = 1 << 28
+    for a in range(0, n + 1, step):                       # offsets in chunks: 0, 1, 3, 5, ..., 2n-3, 2n-2
+        k = torch.arange(a, min(a + step, n + 1), dtype=torch.int64, device="cuda")
+        want = torch.where(k == 0, 0, 2 * k - 1)
+        want[k == n] = 2 * n - 2
+        assert bool((off[a:a + k.numel()] == want).all())
+    del k, want
+    assert int(starts[0]) == 0 and int(starts[-1]) == 1
+    assert bool((starts[1:-1].view(-1, 2) == torch.tensor([0, 1], dtype=torch.int32, device="cuda")).all())
