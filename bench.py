@@ -203,19 +203,21 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = lr.lr_create(local)
+    d_sa = torch.from_numpy(w.sa).to(dev)
     d_rank = torch.from_numpy(w.rank).to(dev)
     d_lcp = torch.from_numpy(w.lcp).to(dev)
     ln = torch.empty(n, dtype=torch.int32, device=dev)
     st = torch.empty(n, dtype=torch.int32, device=dev)
     off = torch.empty(n + 1, dtype=torch.int64, device=dev)
     starts = torch.empty(1, dtype=torch.int32, device=dev)
-    status, total = lr.lr_query_all(ctx, d_rank, d_lcp, ln, st, off, starts, stream)
+    status, total = lr.lr_query_all(ctx, d_sa, None, d_lcp, ln, st, off, starts, stream)
     if status not in (lr.LR_OK, lr.LR_ERR_CAPACITY):
         raise lr.LRError(status, "lr_query_all")
     starts = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    m = lr.lr_last_compact_size(ctx, stream)
 
-    def step():
-        s, _ = lr.lr_query_all(ctx, d_rank, d_lcp, ln, st, off, starts, stream, sync=False)
+    def step(sa=d_sa, rank=None):
+        s, _ = lr.lr_query_all(ctx, sa, rank, d_lcp, ln, st, off, starts, stream, sync=False)
         if s != lr.LR_OK:
             raise lr.LRError(s, "lr_query_all")
 
@@ -248,31 +250,47 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
-    # per-kernel durations (CUDA events on the launching stream, recorded by the library)
-    lr.lr_set_phase_timing(ctx, True)
-    per = None
-    reps = max(3, min(args.steps, 20))
-    for _ in range(reps):
-        step()
-        t = lr.lr_phase_times(ctx)
-        per = [0.0] * len(t) if per is None else per
-        per = [a + b for a, b in zip(per, t)]
-    per = [p / reps for p in per]
-    lr.lr_set_phase_timing(ctx, False)
+    # per-phase durations (CUDA events on the launching stream, recorded by the library)
+    def phase_avg(**kw):
+        lr.lr_set_phase_timing(ctx, True)
+        acc = None
+        reps = max(3, min(args.steps, 20))
+        for _ in range(reps):
+            step(**kw)
+            t = lr.lr_phase_times(ctx)
+            acc = list(t) if acc is None else [a + b for a, b in zip(acc, t)]
+        lr.lr_set_phase_timing(ctx, False)
+        return [a / reps for a in acc]
+
+    per = phase_avg()
+    # the paper's own data flow (rank + random lcp gather), same cover kernel, for comparison
+    for _ in range(2):
+        step(sa=None, rank=d_rank)
+    torch.cuda.synchronize(dev)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    gsteps = max(3, min(args.steps, 10))
+    for _ in range(gsteps):
+        step(sa=None, rank=d_rank)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    gather_ms = g0.elapsed_time(g1) / gsteps
+    per_gather = phase_avg(sa=None, rank=d_rank)
 
     # e2e through the host-buffer entry point, pinned host memory
-    h_rank = torch.from_numpy(w.rank).pin_memory()
+    h_sa = torch.from_numpy(w.sa).pin_memory()
     h_lcp = torch.from_numpy(w.lcp).pin_memory()
     h_ln = torch.empty(n, dtype=torch.int32).pin_memory()
     h_st = torch.empty(n, dtype=torch.int32).pin_memory()
     h_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
     h_starts = torch.empty(max(total, 1), dtype=torch.int32).pin_memory()
     e2e_steps = max(2, min(args.steps, 5))
-    lr.lr_query_all_host(ctx, h_rank, h_lcp, h_ln, h_st, h_off, h_starts, stream)   # warm the buffers
+    lr.lr_query_all_host(ctx, h_sa, None, h_lcp, h_ln, h_st, h_off, h_starts, stream)   # warm the buffers
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        s, tot2 = lr.lr_query_all_host(ctx, h_rank, h_lcp, h_ln, h_st, h_off, h_starts, stream)
+        s, tot2 = lr.lr_query_all_host(ctx, h_sa, None, h_lcp, h_ln, h_st, h_off, h_starts, stream)
         if s != lr.LR_OK or tot2 != total:
             raise lr.LRError(s, "lr_query_all_host")
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
@@ -283,21 +301,22 @@ def run_ours(args):
     lr.lr_destroy(ctx)
 
     if rank == 0:
-        import oracle
         peak, peak_kind = measured_peaks()
-        cs, _ = oracle.compact(w.rank, w.lcp)
-        m = int(cs.size)
-        names = ["k_llr_compact", "k_cover"]
+        names = ["partition", "bucket_llr", "cover"]
+        # bytes each phase has to move in this design: partition: sa + lcp read,
+        # level-1 entries written and read, level-2 entries written; bucket:
+        # entries read, compact LLR's written; cover: compact LLR's read, every
+        # output written once
         algo = {
-            # Lemma 1 inputs (rank, lcp) + the compact LLR array written
-            "k_llr_compact": 8.0 * n + 8.0 * m,
-            # compact LLR array read + lr_len, lr_start, offsets, starts written
-            "k_cover": 8.0 * m + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total,
+            "partition": 4.0 * n + 4.0 * (n + 1) + 12.0 * n,
+            "bucket_llr": 4.0 * n + 8.0 * m,
+            "cover": 8.0 * m + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total,
         }
         dom = int(np.argmax(per))
         kname = names[dom]
         achieved = algo[kname] / (per[dom] * 1e-3) / 1e9
-        path_bytes = 8.0 * n + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
+        # compulsory bytes of the whole query: inputs read once, outputs written once
+        path_bytes = 4.0 * n + 4.0 * (n + 1) + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
         path_achieved = path_bytes / (ms * 1e-3) / 1e9
         value = ws * n / (ms * 1e-3) / 1e9
         rate, block, a0, dt = cpu_oracle_rate(w, args.cpu_seconds)
@@ -309,6 +328,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": n, "parallelism": "replicas" if ws > 1 else "single",
                        "inputs": "rank+lcp resident in HBM (%.2f GiB, larger than the 129 MB L2: no flush)"
                                  % ((8 * n + 4) / 2**30),
+                       "input": "sa+lcp (rank-order front end)",
                        "total_lr_starts": total, "compact_llr": m},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
@@ -318,11 +338,15 @@ def run_ours(args):
                               "frac": round(path_achieved / peak, 4), "peak_kind": peak_kind,
                               "algorithmic_bytes_per_step": path_bytes},
             "kernel_ms": {nm: round(p, 4) for nm, p in zip(names, per)},
+            "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
+                                  "value": round(ws * n / (gather_ms * 1e-3) / 1e9, 3),
+                                  "kernel_ms": {nm: round(p, 4) for nm, p in
+                                                zip(["gather_llr", "cover"], per_gather)}},
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
                                        "[%d, %d) of the same workload, %.1f s single-threaded" % (a0, a0 + block, dt)},
             "e2e": {"value": round(ws * n / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
-                    "h2d_bytes_per_step": 4 * n + 4 * (n + 1),
+                    "h2d_bytes_per_step": 4 * n + 4 * (n + 1),   # sa + lcp
                     "d2h_bytes_per_step": 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8},
             "gpu_launches": launches,
             "clocks": clk,

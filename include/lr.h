@@ -9,12 +9,23 @@
  * "all" calls list every one of them.
  *
  * Inputs are the arrays the paper builds on the host before the query and
- * copies to the GPU (Sec. 4): the rank array and the lcp array of S, here
- * 0-based:
- *   rank[i] = r  iff  sa[r] = i                          (int32, n entries)
+ * copies to the GPU (Sec. 4), here 0-based:
+ *   sa[r]   = start of the r-th smallest suffix                  (int32, n entries)
+ *   rank[i] = r  iff  sa[r] = i                                   (int32, n entries)
  *   lcp[0] = lcp[n] = 0, lcp[r] = |lcp(S[sa[r-1]..], S[sa[r]..])| for 0<r<n
- *                                                         (int32, n+1 entries)
- * The string itself is not needed (Lemma 1 reads only rank and lcp).
+ *                                                                  (int32, n+1 entries)
+ * The string itself is not needed.  Lemma 1 gives the length of the
+ * left-bounded longest repeat at i as L_i = max(lcp[rank[i]], lcp[rank[i]+1]),
+ * which read in rank order is L_{sa[r]} = max(lcp[r], lcp[r+1]).  A query
+ * takes sa or rank (at least one; sa wins when both are given):
+ *   - with sa, the lengths are computed in rank order (sa and lcp read
+ *     once, coalesced) and radix-partitioned back to text order;
+ *   - with rank only, each position gathers its two lcp words, the paper's
+ *     own data flow (Sec. 4): one random 32-byte sector per position.
+ * Both give identical results.  sa must be a permutation of [0, n) and rank
+ * its inverse; a violation that the kernels detect is reported as
+ * LR_ERR_SENTINEL, and no input ever makes a kernel access memory out of
+ * bounds.
  *
  * Outputs, per position k (0-based):
  *   lr_len[k]    length of LR_k, 0 if none                          (int32)
@@ -30,8 +41,9 @@
  *  - Calls are asynchronous on `stream` (NULL = the legacy default stream)
  *    unless they take an h_* output, which makes them wait for the stream.
  *  - The library owns only its scratch (tile status words, the compact LLR
- *    array), cached in the context and grown on demand; a context must not
- *    be used from two host threads at once.
+ *    array, the partition buffers: about 16 bytes per position), cached in
+ *    the context and grown on demand; a context must not be used from two
+ *    host threads at once.
  *  - No C++ exception crosses this interface.  Errors are returned as
  *    lr_status.  Malformed device inputs (a rank outside [0, n), lcp[0] or
  *    lcp[n] not 0) are detected by the kernels, never read out of bounds,
@@ -79,11 +91,11 @@ lr_status lr_device_status(lr_ctx* ctx, lr_stream_t stream);
 /*
  * Leftmost LR of every position (Algorithm 2: compaction of the LLR array,
  * Sec. 3.2, then for each k the longest compact LLR covering k, the leftmost
- * on ties).  d_rank: n int32; d_lcp: n+1 int32; d_lr_start, d_lr_len: n
- * int32 outputs.  Asynchronous.
+ * on ties).  d_sa, d_rank: n int32 (one may be NULL); d_lcp: n+1 int32;
+ * d_lr_start, d_lr_len: n int32 outputs.  Asynchronous.
  */
 lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream,
-                            const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                            const int32_t* d_sa, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
                             int32_t* d_lr_start, int32_t* d_lr_len);
 
 /*
@@ -101,13 +113,13 @@ lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream,
  *                   lr_device_status() later.
  */
 lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream,
-                       const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                       const int32_t* d_sa, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
                        int32_t* d_lr_len, int32_t* d_lr_start,
                        int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
                        int64_t* h_total);
 
 /*
- * lr_query_all on host buffers: copies rank and lcp to device memory owned
+ * lr_query_all on host buffers: copies sa (or rank) and lcp to device memory owned
  * by the context, runs the query on `stream`, copies the results back and
  * waits.  h_starts holds starts_capacity entries; *h_total receives the
  * total, and LR_ERR_CAPACITY is returned if it does not fit (the other
@@ -115,14 +127,14 @@ lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream,
  * faster.
  */
 lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
-                            const int32_t* h_rank, const int32_t* h_lcp, int32_t n,
+                            const int32_t* h_sa, const int32_t* h_rank, const int32_t* h_lcp, int32_t n,
                             int32_t* h_lr_len, int32_t* h_lr_start,
                             int64_t* h_offsets, int32_t* h_starts, int64_t starts_capacity,
                             int64_t* h_total);
 
 /*
  * Kernels launched by the most recent query of this context (for the
- * benchmark's launch accounting).
+ * benchmark's launch accounting): 4 with sa, 2 with rank only.
  */
 int32_t lr_last_launch_count(lr_ctx* ctx);
 
@@ -130,12 +142,20 @@ int32_t lr_last_launch_count(lr_ctx* ctx);
  * Per-kernel timing (instrumentation, off by default).  While enabled, each
  * query records a CUDA event on its stream before and after every kernel it
  * launches.  lr_phase_times() waits for the last query's events and writes
- * the duration in milliseconds of each of its kernels, in launch order
- * (k_llr_compact, k_cover), into ms[0 .. cap); it returns the number of
- * kernels of that query, or -1 if timing was off or an event failed.
+ * the duration in milliseconds of each of its phases, in launch order, into
+ * ms[0 .. cap); it returns the number of phases of that query, or -1 if
+ * timing was off or an event failed.  The phases are: with sa, the
+ * partition (two kernels), the bucket front end and the cover kernel;
+ * with rank only, the gather front end and the cover kernel.
  */
 lr_status lr_set_phase_timing(lr_ctx* ctx, int32_t enable);
 int32_t lr_phase_times(lr_ctx* ctx, float* ms, int32_t cap);
+
+/*
+ * Size of the compact LLR array of the context's last query (the number of
+ * useful LLR's, Sec. 3.2), read back after waiting for `stream`.
+ */
+lr_status lr_last_compact_size(lr_ctx* ctx, lr_stream_t stream, int64_t* m);
 
 #ifdef __cplusplus
 }

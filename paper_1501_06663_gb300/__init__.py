@@ -30,7 +30,7 @@ LR_ERR_BUSY = 7
 EXPORTED = (
     "lr_create", "lr_destroy", "lr_status_str", "lr_last_cuda_error", "lr_device_status",
     "lr_query_leftmost", "lr_query_all", "lr_query_all_host", "lr_last_launch_count",
-    "lr_set_phase_timing", "lr_phase_times",
+    "lr_set_phase_timing", "lr_phase_times", "lr_last_compact_size",
 )
 
 
@@ -56,14 +56,15 @@ def load(path: str | None = None):
     lib.lr_status_str.restype = ctypes.c_char_p
     lib.lr_last_cuda_error.argtypes = [vp, ctypes.POINTER(ci)]
     lib.lr_device_status.argtypes = [vp, vp]
-    lib.lr_query_leftmost.argtypes = [vp, vp, vp, vp, i32, vp, vp]
-    lib.lr_query_all.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
-    lib.lr_query_all_host.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_query_leftmost.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp]
+    lib.lr_query_all.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_query_all_host.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.lr_last_launch_count.argtypes = [vp]
     lib.lr_last_launch_count.restype = i32
     lib.lr_set_phase_timing.argtypes = [vp, i32]
     lib.lr_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
     lib.lr_phase_times.restype = i32
+    lib.lr_last_compact_size.argtypes = [vp, vp, ctypes.POINTER(i64)]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -136,28 +137,44 @@ def lr_phase_times(ctx, cap: int = 8):
     return None if k < 0 else [float(buf[i]) for i in range(min(k, cap))]
 
 
-def lr_query_leftmost(ctx, rank, lcp, lr_start, lr_len, stream=None) -> int:
-    n = int(rank.numel())
-    return load().lr_query_leftmost(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n,
+def _n_of(sa, rank):
+    t = sa if sa is not None else rank
+    if hasattr(t, "numel"):
+        return int(t.numel())
+    return int(t.size)
+
+
+def lr_last_compact_size(ctx, stream=None) -> int:
+    """Number of useful LLR's (compact LLR array size) of the context's last query."""
+    m = ctypes.c_int64(-1)
+    _check(load().lr_last_compact_size(ctx, _stream(stream), ctypes.byref(m)), "lr_last_compact_size")
+    return m.value
+
+
+def lr_query_leftmost(ctx, sa, rank, lcp, lr_start, lr_len, stream=None) -> int:
+    """sa or rank may be None (not both); sa is used when given."""
+    n = _n_of(sa, rank)
+    return load().lr_query_leftmost(ctx, _stream(stream), _ptr(sa), _ptr(rank), _ptr(lcp), n,
                                     _ptr(lr_start), _ptr(lr_len))
 
 
-def lr_query_all(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
-    """Returns (status, total or None)."""
-    n = int(rank.numel())
+def lr_query_all(ctx, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
+    """Device buffers; sa or rank may be None (not both).  Returns (status, total or None)."""
+    n = _n_of(sa, rank)
     cap = int(starts.numel()) if starts is not None else 0
     tot = ctypes.c_int64(-1)
-    st = load().lr_query_all(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len), _ptr(lr_start),
-                             _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot) if sync else None)
+    st = load().lr_query_all(ctx, _stream(stream), _ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(lr_len),
+                             _ptr(lr_start), _ptr(offsets), _ptr(starts), cap,
+                             ctypes.byref(tot) if sync else None)
     return st, (tot.value if sync else None)
 
 
-def lr_query_all_host(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None):
-    """Host (numpy or CPU tensor) buffers.  Returns (status, total)."""
-    n = int(rank.size if hasattr(rank, "size") and not callable(rank.size) else rank.numel())
+def lr_query_all_host(ctx, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream=None):
+    """Host (numpy or CPU tensor) buffers; sa or rank may be None.  Returns (status, total)."""
+    n = _n_of(sa, rank)
     cap = int(len(starts)) if starts is not None else 0
     tot = ctypes.c_int64(-1)
-    st = load().lr_query_all_host(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len),
+    st = load().lr_query_all_host(ctx, _stream(stream), _ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(lr_len),
                                   _ptr(lr_start), _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot))
     return st, tot.value
 
@@ -183,28 +200,31 @@ class Context:
         except Exception:
             pass
 
-    def query_leftmost(self, rank, lcp, stream=None):
+    def query_leftmost(self, lcp, sa=None, rank=None, stream=None):
+        """Leftmost LR per position: (lr_start, lr_len).  Give sa or rank (device tensors)."""
         import torch
-        n = int(rank.numel())
-        lr_start = torch.empty(n, dtype=torch.int32, device=rank.device)
-        lr_len = torch.empty(n, dtype=torch.int32, device=rank.device)
-        _check(lr_query_leftmost(self.handle, rank, lcp, lr_start, lr_len, stream), "lr_query_leftmost")
+        t = sa if sa is not None else rank
+        n = int(t.numel())
+        lr_start = torch.empty(n, dtype=torch.int32, device=t.device)
+        lr_len = torch.empty(n, dtype=torch.int32, device=t.device)
+        _check(lr_query_leftmost(self.handle, sa, rank, lcp, lr_start, lr_len, stream), "lr_query_leftmost")
         _check(lr_device_status(self.handle, stream), "lr_query_leftmost (device)")
         return lr_start, lr_len
 
-    def query_all(self, rank, lcp, capacity: int | None = None, stream=None):
-        """All LR's as CSR: (lr_len, lr_start, offsets, starts[:total])."""
+    def query_all(self, lcp, sa=None, rank=None, capacity: int | None = None, stream=None):
+        """All LR's as CSR: (lr_len, lr_start, offsets, starts[:total]).  Give sa or rank."""
         import torch
-        n = int(rank.numel())
-        dev = rank.device
+        t = sa if sa is not None else rank
+        n = int(t.numel())
+        dev = t.device
         lr_len = torch.empty(n, dtype=torch.int32, device=dev)
         lr_start = torch.empty(n, dtype=torch.int32, device=dev)
         offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
         cap = 2 * n + 1024 if capacity is None else int(capacity)
         starts = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
-        st, total = lr_query_all(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+        st, total = lr_query_all(self.handle, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream)
         if st == LR_ERR_CAPACITY:
             starts = torch.empty(total, dtype=torch.int32, device=dev)
-            st, total = lr_query_all(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+            st, total = lr_query_all(self.handle, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream)
         _check(st, "lr_query_all")
         return lr_len, lr_start, offsets, starts[:total]

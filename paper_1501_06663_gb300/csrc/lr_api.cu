@@ -14,12 +14,14 @@ struct lr_ctx {
     int last_cuda_error = 0;
     int last_launches = 0;
     unsigned* d_err = nullptr;            // sticky device error bits
-    unsigned char* scratch = nullptr;     // TileScratch storage
+    unsigned char* scratch = nullptr;     // lr::Scratch storage
     size_t scratch_bytes = 0;
     long long scratch_n = 0;              // positions the scratch is laid out for
     long long* h_pinned = nullptr;        // [0] total, [1] error bits
     unsigned char* hostpath = nullptr;    // device buffers of lr_query_all_host
     size_t hostpath_bytes = 0;
+    int sms = 0;                          // SM count of the device
+    long long last_n = 0;                 // size of the last query (its tile_cbase[ntiles] is m)
     lr::PhaseEvents events;               // per-kernel timing (off by default)
     bool events_created = false;
 };
@@ -50,24 +52,32 @@ lr_status cuda_fail(lr_ctx* ctx, cudaError_t e) {
 }
 
 struct Layout {
-    size_t off_status_c, off_status_o, zero_end, off_cbase, off_cstart, off_cend, total;
+    size_t off_status_g, off_status_b, off_status_o, off_cursor1, off_cursor2, zero_end;
+    size_t off_tile_cbase, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo, total;
 };
 
 Layout layout_for(long long n) {
-    const long long nt = lr::num_tiles(n);
+    const long long nt = lr::num_tiles(n), nb = lr::num_buckets(n), ns = lr::num_supers(n);
     Layout L;
-    L.off_status_c = kAlign;                       // tickets in [0, 8), per-query error bits at 16
-    L.off_status_o = align_up(L.off_status_c + (size_t)nt * 8);
-    L.zero_end = L.off_status_o + (size_t)nt * 8;
-    L.off_cbase = align_up(L.zero_end);
-    L.off_cstart = align_up(L.off_cbase + (size_t)(nt + 1) * 4);
+    L.off_status_g = kAlign;                       // tickets in [0, 16), per-query error bits at 16
+    L.off_status_b = align_up(L.off_status_g + (size_t)nt * 8);
+    L.off_status_o = align_up(L.off_status_b + (size_t)nb * 8);
+    L.off_cursor1 = align_up(L.off_status_o + (size_t)nt * 8);
+    L.off_cursor2 = align_up(L.off_cursor1 + (size_t)ns * 4 * lr::kCursorStride);
+    L.zero_end = L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride;
+    L.off_tile_cbase = align_up(L.zero_end);
+    L.off_cstart = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
     L.off_cend = align_up(L.off_cstart + (size_t)n * 4);
-    L.total = align_up(L.off_cend + (size_t)n * 4);
+    L.off_ent1 = align_up(L.off_cend + (size_t)n * 4);
+    L.off_ent2 = align_up(L.off_ent1 + (size_t)ns * lr::kSuper * 4);
+    L.off_lbig = align_up(L.off_ent2 + (size_t)nb * lr::kBucket * 4);
+    L.off_halo = align_up(L.off_lbig + (size_t)n * 4);
+    L.total = align_up(L.off_halo + (size_t)(nb + 1) * 4);
     return L;
 }
 
 // Grows the scratch to hold a query of n positions and fills `s`.
-lr_status get_scratch(lr_ctx* ctx, long long n, lr::TileScratch* s) {
+lr_status get_scratch(lr_ctx* ctx, long long n, lr::Scratch* s) {
     if (n > ctx->scratch_n) {
         const Layout L = layout_for(n);
         if (ctx->scratch) {
@@ -83,20 +93,31 @@ lr_status get_scratch(lr_ctx* ctx, long long n, lr::TileScratch* s) {
         ctx->scratch_bytes = L.total;
         ctx->scratch_n = n;
     }
+    // the regions are laid out for scratch_n; a smaller query uses their prefixes
     const Layout L = layout_for(ctx->scratch_n);
-    const long long nt = lr::num_tiles(n);
     unsigned char* b = ctx->scratch;
+    const long long nt = lr::num_tiles(n), nb = lr::num_buckets(n), ns = lr::num_supers(n);
     s->tickets = (unsigned*)b;
     s->qerr = (unsigned*)(b + 16);
     s->err = ctx->d_err;
-    s->status_c = (unsigned long long*)(b + L.off_status_c);
+    s->status_g = (unsigned long long*)(b + L.off_status_g);
+    s->status_b = (unsigned long long*)(b + L.off_status_b);
     s->status_o = (unsigned long long*)(b + L.off_status_o);
-    s->cbase = (int32_t*)(b + L.off_cbase);
+    s->cursor1 = (unsigned*)(b + L.off_cursor1);
+    s->cursor2 = (unsigned*)(b + L.off_cursor2);
+    s->tile_cbase = (int32_t*)(b + L.off_tile_cbase);
     s->cstart = (int32_t*)(b + L.off_cstart);
     s->cend = (int32_t*)(b + L.off_cend);
+    s->ent1 = (uint32_t*)(b + L.off_ent1);
+    s->ent2 = (uint32_t*)(b + L.off_ent2);
+    s->lbig = (int32_t*)(b + L.off_lbig);
+    s->halo = (int32_t*)(b + L.off_halo);
     s->ntiles = nt;
+    s->nbuckets = nb;
+    s->nsupers = ns;
     s->zero_base = b;
-    s->zero_bytes = L.off_status_o + (size_t)nt * 8;
+    s->zero_bytes = L.zero_end;          // covers the status words and cursors of any n <= scratch_n
+    ctx->last_n = n;
     return LR_OK;
 }
 
@@ -154,6 +175,7 @@ lr_status lr_create(lr_ctx** out, int device) {
     ctx->device = device;
     DeviceGuard g(device);
     cudaError_t e = g.ok ? cudaSuccess : cudaErrorInvalidDevice;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = lr::configure_kernels();
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, 256);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, 256);
@@ -208,10 +230,23 @@ lr_status lr_set_phase_timing(lr_ctx* ctx, int32_t enable) {
     return LR_OK;
 }
 
-int32_t lr_phase_times(lr_ctx* ctx, float* ms, int32_t cap) {
-    if (!ctx || !ctx->events.enabled || ctx->last_launches <= 0) return -1;
+lr_status lr_last_compact_size(lr_ctx* ctx, lr_stream_t stream, int64_t* m) {
+    if (!ctx || !m || ctx->last_n <= 0 || !ctx->scratch) return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
-    const int nk = ctx->last_launches;
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    const Layout L = layout_for(ctx->scratch_n);
+    const int32_t* src = (const int32_t*)(ctx->scratch + L.off_tile_cbase) + lr::num_tiles(ctx->last_n);
+    cudaError_t e = cudaMemcpyAsync(&ctx->h_pinned[2], src, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    *m = (int64_t)(*(int32_t*)&ctx->h_pinned[2]);
+    return LR_OK;
+}
+
+int32_t lr_phase_times(lr_ctx* ctx, float* ms, int32_t cap) {
+    if (!ctx || !ctx->events.enabled || ctx->events.count <= 0) return -1;
+    DeviceGuard g(ctx->device);
+    const int nk = ctx->events.count;
     if (cudaEventSynchronize(ctx->events.ev[nk]) != cudaSuccess) return -1;
     for (int i = 0; i < nk && i < cap; ++i) {
         float t = 0.f;
@@ -228,32 +263,32 @@ lr_status lr_device_status(lr_ctx* ctx, lr_stream_t stream) {
     return sync_total(ctx, (cudaStream_t)stream, nullptr, nullptr);
 }
 
-lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp,
-                            int32_t n, int32_t* d_lr_start, int32_t* d_lr_len) {
-    if (!ctx || !d_rank || !d_lcp || !d_lr_start || !d_lr_len) return LR_ERR_ARG;
+lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa, const int32_t* d_rank,
+                            const int32_t* d_lcp, int32_t n, int32_t* d_lr_start, int32_t* d_lr_len) {
+    if (!ctx || (!d_sa && !d_rank) || !d_lcp || !d_lr_start || !d_lr_len) return LR_ERR_ARG;
     if (check_n(n) != LR_OK) return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
-    lr::TileScratch s;
+    lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
-    cudaError_t e = lr::launch_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
+    cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
                                      (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
     return e == cudaSuccess ? LR_OK : cuda_fail(ctx, e);
 }
 
-lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
-                       int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
-                       int64_t starts_capacity, int64_t* h_total) {
-    if (!ctx || !d_rank || !d_lcp || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
+lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa, const int32_t* d_rank,
+                       const int32_t* d_lcp, int32_t n, int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets,
+                       int32_t* d_starts, int64_t starts_capacity, int64_t* h_total) {
+    if (!ctx || (!d_sa && !d_rank) || !d_lcp || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
     if (starts_capacity < 0 || (starts_capacity > 0 && !d_starts)) return LR_ERR_ARG;
     if (check_n(n) != LR_OK) return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
-    lr::TileScratch s;
+    lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
-    cudaError_t e = lr::launch_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
+    cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
                                      starts_capacity, true, (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     if (!h_total) return LR_OK;
@@ -262,10 +297,10 @@ lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, c
     return (*h_total > starts_capacity) ? LR_ERR_CAPACITY : LR_OK;
 }
 
-lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_rank, const int32_t* h_lcp,
-                            int32_t n, int32_t* h_lr_len, int32_t* h_lr_start, int64_t* h_offsets,
-                            int32_t* h_starts, int64_t starts_capacity, int64_t* h_total) {
-    if (!ctx || !h_rank || !h_lcp || !h_lr_len || !h_lr_start || !h_offsets || !h_total) return LR_ERR_ARG;
+lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_sa, const int32_t* h_rank,
+                            const int32_t* h_lcp, int32_t n, int32_t* h_lr_len, int32_t* h_lr_start,
+                            int64_t* h_offsets, int32_t* h_starts, int64_t starts_capacity, int64_t* h_total) {
+    if (!ctx || (!h_sa && !h_rank) || !h_lcp || !h_lr_len || !h_lr_start || !h_offsets || !h_total) return LR_ERR_ARG;
     if (starts_capacity < 0 || (starts_capacity > 0 && !h_starts)) return LR_ERR_ARG;
     if (check_n(n) != LR_OK) return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
@@ -289,19 +324,20 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_ra
         ctx->hostpath_bytes = need;
     }
     unsigned char* b = ctx->hostpath;
-    int32_t* d_rank = (int32_t*)(b + o_rank);
+    int32_t* d_in = (int32_t*)(b + o_rank);            // sa, or rank when no sa is given
     int32_t* d_lcp = (int32_t*)(b + o_lcp);
     int32_t* d_len = (int32_t*)(b + o_len);
     int32_t* d_start = (int32_t*)(b + o_start);
     int64_t* d_off = (int64_t*)(b + o_off);
     int32_t* d_starts = (int32_t*)(b + o_starts);
-    e = cudaMemcpyAsync(d_rank, h_rank, nn * 4, cudaMemcpyHostToDevice, strm);
+    e = cudaMemcpyAsync(d_in, h_sa ? h_sa : h_rank, nn * 4, cudaMemcpyHostToDevice, strm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_lcp, h_lcp, (nn + 1) * 4, cudaMemcpyHostToDevice, strm);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
-    lr::TileScratch s;
+    lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
-    e = lr::launch_query(d_rank, d_lcp, n, s, d_len, d_start, d_off, d_starts, starts_capacity, true, strm,
+    e = lr::launch_query(h_sa ? d_in : nullptr, h_sa ? nullptr : d_in, d_lcp, n, s, d_len, d_start, d_off, d_starts,
+                         starts_capacity, true, strm,
                          &ctx->last_launches, &ctx->events);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_lr_len, d_len, nn * 4, cudaMemcpyDeviceToHost, strm);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_lr_start, d_start, nn * 4, cudaMemcpyDeviceToHost, strm);

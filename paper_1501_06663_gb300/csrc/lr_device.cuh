@@ -35,6 +35,10 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & (kWarp - 1); }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
@@ -53,39 +57,41 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-// Called by one whole warp of the tile.  Publishes `aggregate` for `tile`,
-// sums the totals of all earlier tiles by looking back over their status
-// words, publishes the inclusive prefix and returns the exclusive one (the
-// same value in every lane).  Waits only on earlier tiles, which were
-// scheduled before this one, and gives up (setting kErrTimeout in *err and
-// *qerr) after kSpinLimit polls of any one word.
-__device__ inline long long lookback_exclusive(unsigned long long* status, long long tile,
-                                               long long aggregate, unsigned* err, unsigned* qerr) {
-    const unsigned lane = lane_id();
-    if (tile == 0) {
-        if (lane == 0) st_release(&status[0], (kPrefix << kFlagShift) | (unsigned long long)aggregate);
-        return 0;
+// Polls `w` until its flag is set; after kSpinLimit polls records a timeout
+// in both error words and returns a prefix of 0 so the caller can finish.
+__device__ __forceinline__ unsigned long long wait_flag(const unsigned long long* w, unsigned* err, unsigned* qerr) {
+    unsigned long long v = ld_acquire(w);
+    int polls = 0;
+    while ((v >> kFlagShift) == 0) {
+        if (++polls >= kSpinLimit) {
+            atomicOr(err, kErrTimeout);
+            atomicOr(qerr, kErrTimeout);
+            return kPrefix << kFlagShift;
+        }
+        __nanosleep(32);
+        v = ld_acquire(w);
     }
-    if (lane == 0) st_release(&status[tile], (kAggregate << kFlagShift) | (unsigned long long)aggregate);
+    return v;
+}
+
+__device__ __forceinline__ void publish(unsigned long long* status, long long tile, unsigned long long flag,
+                                        long long value) {
+    st_release(&status[tile], (flag << kFlagShift) | (unsigned long long)value);
+}
+
+// Called by one whole warp after the tile published its aggregate.  Sums the
+// totals of all earlier tiles by looking back over their status words and
+// returns that exclusive prefix (the same value in every lane); it does not
+// publish the inclusive prefix.  Waits only on earlier tiles, which were
+// scheduled before this one.
+__device__ __forceinline__ long long lookback(const unsigned long long* status, long long tile, unsigned* err,
+                                              unsigned* qerr) {
+    const unsigned lane = lane_id();
     long long exclusive = 0;
     long long base = tile - 1;
-    while (true) {
+    while (base >= 0) {
         const long long t = base - (long long)lane;
-        unsigned long long w = (kPrefix << kFlagShift);   // before tile 0: prefix 0
-        if (t >= 0) {
-            int polls = 0;
-            w = ld_acquire(&status[t]);
-            while ((w >> kFlagShift) == 0) {
-                if (++polls >= kSpinLimit) {
-                    atomicOr(err, kErrTimeout);
-                    atomicOr(qerr, kErrTimeout);
-                    w = (kPrefix << kFlagShift);
-                    break;
-                }
-                __nanosleep(64);
-                w = ld_acquire(&status[t]);
-            }
-        }
+        const unsigned long long w = (t >= 0) ? wait_flag(&status[t], err, qerr) : (kPrefix << kFlagShift);
         const unsigned pmask = __ballot_sync(kFull, (w >> kFlagShift) == kPrefix);
         const int stop = pmask ? __ffs(pmask) - 1 : kWarp - 1;
         const long long contrib = ((int)lane <= stop) ? (long long)(w & kValMask) : 0;
@@ -93,8 +99,18 @@ __device__ inline long long lookback_exclusive(unsigned long long* status, long 
         if (pmask) break;
         base -= kWarp;
     }
-    if (lane == 0) st_release(&status[tile], (kPrefix << kFlagShift) | (unsigned long long)(exclusive + aggregate));
     return exclusive;
+}
+
+// Publish-aggregate, look back, publish-prefix in one call (one whole warp).
+__device__ __forceinline__ long long lookback_exclusive(unsigned long long* status, long long tile,
+                                                       long long aggregate, unsigned* err, unsigned* qerr) {
+    const unsigned lane = lane_id();
+    if (lane == 0) publish(status, tile, tile == 0 ? kPrefix : kAggregate, aggregate);
+    if (tile == 0) return 0;
+    const long long ex = lookback(status, tile, err, qerr);
+    if (lane == 0) publish(status, tile, kPrefix, ex + aggregate);
+    return ex;
 }
 
 }  // namespace lr

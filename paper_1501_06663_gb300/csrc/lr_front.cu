@@ -1,0 +1,470 @@
+// Front ends of the longest-repeat query: they turn the input arrays into
+// the compact LLR array LLRc (Sec. 3.2 / Sec. 4.2.1 of Tian and Xu, arXiv
+// 1501.06663): every position i with L_i > 0 and L_i >= L_{i-1}, in
+// ascending i, as cstart[t] = i, cend[t] = i + L_i - 1, where
+// L_i = max(lcp[rank[i]], lcp[rank[i]+1]) (Lemma 1).  They also record, for
+// every tile of kTile positions, the index of its first LLRc entry
+// (tile_cbase), which the cover kernel starts from.
+//
+// Two front ends compute the same LLRc:
+//
+//  * rank-order (the default when the suffix array is given).  Lemma 1 read
+//    in rank order is L_{sa[r]} = max(lcp[r], lcp[r+1]): sa and lcp are then
+//    read once, coalesced, instead of one random lcp sector per position.
+//    k_part1 and k_part2 radix-partition the pairs <sa[r], L_{sa[r]}> by
+//    the position, first into super-buckets of 2^20 positions, then into
+//    buckets of 2^15 (packed 4-byte entries; a length of 4095 or more goes
+//    to lbig).  k_bucket_llr then loads one bucket per
+//    CTA, scatters its lengths into shared memory by position, and flags
+//    and compacts them.
+//
+//  * rank gather (when only rank is given, as in the paper's data flow of
+//    Sec. 4): k_gather_llr reads rank coalesced and gathers the two lcp
+//    words of each position, then flags and compacts one tile.
+//
+// Both place their entries in LLRc with a decoupled look-back over the
+// per-CTA counts (tiles handed out in order by an atomic ticket).
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "lr_device.cuh"
+#include "lr_internal.h"
+
+namespace lr {
+
+namespace {
+
+__device__ __forceinline__ void report(const Scratch& s, unsigned bits) {
+    atomicOr(s.err, bits);
+    atomicOr(s.qerr, bits);
+}
+
+// Exclusive scan of 64 ints by one warp (two per lane); returns the total.
+__device__ __forceinline__ int warp_scan64(int32_t* a) {
+    const int lane = lane_id();
+    const int x = a[2 * lane], y = a[2 * lane + 1];
+    const int incl = warp_incl_scan(x + y);
+    a[2 * lane] = incl - x - y;
+    a[2 * lane + 1] = incl - y;
+    return __shfl_sync(kFull, incl, kWarp - 1);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// rank gather front end
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads)
+k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, int32_t n, Scratch s) {
+    constexpr int kChunks = kTile / kWarp;          // 64 runs of 32 positions
+    constexpr int kWarps = kThreads / kWarp;        // 8
+    __shared__ int32_t Ls[kTile + 1];               // Ls[0] = L_{k0-1}, Ls[1+x] = L_{k0+x}
+    __shared__ int32_t chunk[kChunks];
+    __shared__ int32_t c_s[kTile];
+    __shared__ int32_t c_e[kTile];
+    __shared__ long long tile_s, base_s;
+    __shared__ int32_t total_s;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) tile_s = atomicAdd(&s.tickets[0], 1u);
+    __syncthreads();
+    const long long tile = tile_s;
+    const long long k0 = tile * kTile;
+
+    // Lemma 1.  rank is streamed; the lcp pair goes through L1 (one sector
+    // for 7 of 8 rank values).  Invalid input is reported and clamped so
+    // every access stays in bounds.
+    unsigned bad = 0;
+    auto llr = [&](long long k) -> int32_t {
+        uint32_t r = (uint32_t)__ldcs(rank + k);
+        if (r >= (uint32_t)n) { bad = 1; r = 0; }
+        const int32_t a = __ldg(lcp + r), b = __ldg(lcp + r + 1);
+        int32_t L = a > b ? a : b;
+        if (L < 0 || (long long)L > (long long)n - k) { bad = 1; L = 0; }
+        return L;
+    };
+#pragma unroll
+    for (int j = 0; j < kTile / kThreads; ++j) {
+        const int x = j * kThreads + tid;
+        Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
+    }
+    if (tid == 0) {
+        Ls[0] = (k0 > 0) ? llr(k0 - 1) : 0;
+        if (tile == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
+    }
+    if (bad) report(s, kErrInput);
+    __syncthreads();
+
+    // K1 flags by warp ballots over runs of 32 positions, K2 within the tile.
+    unsigned masks[kChunks / kWarps];
+#pragma unroll
+    for (int q = 0; q < kChunks / kWarps; ++q) {
+        const int c = q * kWarps + warp;
+        const int x = c * kWarp + lane;
+        const int32_t L = Ls[1 + x], prev = Ls[x];
+        masks[q] = __ballot_sync(kFull, (k0 + x < n) && L > 0 && L >= prev);
+        if (lane == 0) chunk[c] = __popc(masks[q]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int tot = warp_scan64(chunk);
+        if (lane == 0) total_s = tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kChunks / kWarps; ++q) {
+        const int c = q * kWarps + warp;
+        const int x = c * kWarp + lane;
+        if ((masks[q] >> lane) & 1u) {
+            const int o = chunk[c] + __popc(masks[q] & ((1u << lane) - 1u));
+            c_s[o] = (int32_t)(k0 + x);
+            c_e[o] = (int32_t)(k0 + x + Ls[1 + x] - 1);
+        }
+    }
+    // K3: the tile's place in LLRc.
+    if (warp == 0) {
+        const long long ex = lookback_exclusive(s.status_g, tile, total_s, s.err, s.qerr);
+        if (lane == 0) {
+            base_s = ex;
+            s.tile_cbase[tile] = (int32_t)ex;
+            if (tile == s.ntiles - 1) s.tile_cbase[s.ntiles] = (int32_t)(ex + total_s);
+        }
+    }
+    __syncthreads();
+    const long long base = base_s;
+    const int total = total_s;
+    for (int i = tid; i < total; i += kThreads) {
+        s.cstart[base + i] = c_s[i];
+        s.cend[base + i] = c_e[i];
+    }
+}
+
+void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream) {
+    k_gather_llr<<<(unsigned)s.ntiles, kThreads, 0, stream>>>(rank, lcp, n, s);
+}
+
+// ---------------------------------------------------------------------------
+// rank-order front end
+// ---------------------------------------------------------------------------
+
+// Shared memory of a partition CTA: per-bucket counters and the round's
+// entries staged in bucket order, so that each warp store writes one
+// contiguous run.
+struct PartSmem {
+    uint32_t* hist;      // nb: entries of the round per bucket, then slot counters
+    uint32_t* base;      // nb: the round's reserved offset in each bucket
+    uint32_t* loff;      // nb + 1: exclusive prefix of hist (staging offsets)
+    uint32_t* stage;     // kPartRound entries in bucket order
+    uint16_t* sbk;       // kPartRound bucket ids of stage[]
+};
+
+__device__ __forceinline__ PartSmem part_smem(unsigned char* raw, int nb) {
+    PartSmem p;
+    p.hist = reinterpret_cast<uint32_t*>(raw);
+    p.base = p.hist + nb;
+    p.loff = p.base + nb;
+    p.stage = p.loff + nb + 1;
+    p.sbk = reinterpret_cast<uint16_t*>(p.stage + kPartRound);
+    return p;
+}
+
+size_t part_smem_bytes(int nb) { return (size_t)(3 * nb + 1) * 4 + (size_t)kPartRound * 6; }
+
+// Exclusive scan of hist[0..nb) into loff[0..nb] by the whole CTA
+// (kPartThreads threads, nb <= 2 * kPartThreads), and one global atomic per
+// non-empty bucket to reserve the round's room: base[b] = old cursor.
+__device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned* cursor) {
+    __shared__ uint32_t wsum[kPartThreads / kWarp];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t a = (2 * tid < nb) ? p.hist[2 * tid] : 0u;
+    const uint32_t c = (2 * tid + 1 < nb) ? p.hist[2 * tid + 1] : 0u;
+    const int incl = warp_incl_scan((int)(a + c));
+    if (lane == kWarp - 1) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int v = (lane < kPartThreads / kWarp) ? (int)wsum[lane] : 0;
+        const int wi = warp_incl_scan(v);
+        if (lane < kPartThreads / kWarp) wsum[lane] = wi - v;
+        if (lane == kWarp - 1) p.loff[nb] = wi;
+    }
+    __syncthreads();
+    const uint32_t ex = wsum[warp] + incl - a - c;
+    if (2 * tid < nb) {
+        p.loff[2 * tid] = ex;
+        if (a) p.base[2 * tid] = atomicAdd(cursor + (size_t)(2 * tid) * kCursorStride, a);
+    }
+    if (2 * tid + 1 < nb) {
+        p.loff[2 * tid + 1] = ex + a;
+        if (c) p.base[2 * tid + 1] = atomicAdd(cursor + (size_t)(2 * tid + 1) * kCursorStride, c);
+    }
+}
+
+// Level 1: Lemma 1 in rank order, then the partition of the packed entries
+// <position mod 2^20, min(L, 4095)> into super-buckets of 2^20 positions.
+// Each CTA takes kPartRound consecutive ranks, counts them per super-bucket
+// in shared memory, reserves room with one global atomic per touched
+// super-bucket (cursors one cache line apart) and writes its entries in
+// bucket order.  A length of 4095 or more is stored in lbig (field 4095);
+// the length of the last position of every bucket goes to halo (the next
+// bucket's predecessor).
+__global__ void __launch_bounds__(kPartThreads, 2)
+k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = (int)s.nsupers;                    // <= 2048
+    const PartSmem P = part_smem(smem_raw, nb);
+    for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
+    __syncthreads();
+    const long long r0 = (long long)blockIdx.x * kPartRound;
+    unsigned bad = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
+    uint32_t p[kPartPer];
+    int32_t L[kPartPer];
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const long long r = r0 + (long long)j * kPartThreads + threadIdx.x;
+        if (r < n) {
+            p[j] = (uint32_t)__ldcs(sa + r);
+            const int32_t a = __ldcs(lcp + r), c = __ldg(lcp + r + 1);
+            L[j] = a > c ? a : c;
+        } else {
+            p[j] = 0xffffffffu; L[j] = 0;
+        }
+    }
+    uint32_t ent[kPartPer], key[kPartPer];          // key: bucket << 16 | slot, or ~0u
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const long long r = r0 + (long long)j * kPartThreads + threadIdx.x;
+        key[j] = 0xffffffffu;
+        if (r >= n) continue;
+        const uint32_t pj = p[j];
+        if (pj >= (uint32_t)n) { bad = 1; continue; }
+        int32_t Lj = L[j];
+        if (Lj < 0 || (long long)Lj > (long long)n - pj) { bad = 1; Lj = 0; }
+        uint32_t field = (uint32_t)Lj;
+        if (field >= kEsc12) { field = kEsc12; s.lbig[pj] = Lj; }
+        if ((pj & (kBucket - 1)) == kBucket - 1) s.halo[(pj >> kBucketLog) + 1] = Lj;
+        const uint32_t b1 = pj >> kSuperLog;
+        ent[j] = ((pj & (kSuper - 1)) << 12) | field;
+        key[j] = (b1 << 16) | atomicAdd(&P.hist[b1], 1u);
+    }
+    __syncthreads();
+    part_reserve(P, nb, s.cursor1);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        if (key[j] == 0xffffffffu) continue;
+        const uint32_t b1 = key[j] >> 16;
+        const uint32_t o = P.loff[b1] + (key[j] & 0xffffu);
+        P.stage[o] = ent[j];
+        P.sbk[o] = (uint16_t)b1;
+    }
+    __syncthreads();
+    const uint32_t total = P.loff[nb];
+    for (uint32_t i = threadIdx.x; i < total; i += kPartThreads) {
+        const uint32_t b1 = P.sbk[i];
+        const uint32_t idx = P.base[b1] + (i - P.loff[b1]);
+        if (idx < (uint32_t)kSuper) s.ent1[((size_t)b1 << kSuperLog) + idx] = P.stage[i];
+        else bad = 1;                                   // more than 2^20 positions: sa is not a permutation
+    }
+    if (bad) report(s, kErrInput);
+}
+
+// Level 2: each CTA takes kPartRound entries of one super-bucket and splits
+// them into its kSubPerSuper buckets, entries <position mod 2^15, field>
+// (field = L, or kEsc17 when L is in lbig), the same way as level 1.
+__global__ void __launch_bounds__(kPartThreads, 2)
+k_part2(int32_t n, Scratch s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PartSmem P = part_smem(smem_raw, kSubPerSuper);
+    constexpr int kChunksPerSuper = kSuper / kPartRound;
+    const long long b1 = blockIdx.x / kChunksPerSuper;
+    const int q = blockIdx.x % kChunksPerSuper;
+    const uint32_t fill = __ldcg(s.cursor1 + (size_t)b1 * kCursorStride);
+    if (threadIdx.x < kSubPerSuper) P.hist[threadIdx.x] = 0;
+    if (q == 0 && threadIdx.x == 0) {
+        const long long want = ((long long)n - b1 * kSuper < kSuper) ? (long long)n - b1 * kSuper : kSuper;
+        if ((long long)fill != want) report(s, kErrInput);
+    }
+    __syncthreads();
+    const uint32_t i0 = (uint32_t)q * kPartRound;
+    if (i0 >= fill) return;                             // uniform over the CTA
+    const uint32_t* src = s.ent1 + ((size_t)b1 << kSuperLog);
+    uint32_t ent[kPartPer], key[kPartPer];
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
+        ent[j] = (i < fill) ? __ldcs(src + i) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
+        key[j] = 0xffffffffu;
+        if (i >= fill) continue;
+        const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
+        const uint32_t b2 = low20 >> kBucketLog;
+        ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
+        key[j] = (b2 << 16) | atomicAdd(&P.hist[b2], 1u);
+    }
+    __syncthreads();
+    const long long bb = b1 * kSubPerSuper;
+    const int nsub = (int)((s.nbuckets - bb < kSubPerSuper) ? s.nbuckets - bb : kSubPerSuper);
+    part_reserve(P, nsub, s.cursor2 + (size_t)bb * kCursorStride);
+    __syncthreads();
+    unsigned bad = 0;
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        if (key[j] == 0xffffffffu) continue;
+        const uint32_t b2 = key[j] >> 16;
+        if ((int)b2 >= nsub) { bad = 1; continue; }
+        const uint32_t o = P.loff[b2] + (key[j] & 0xffffu);
+        P.stage[o] = ent[j];
+        P.sbk[o] = (uint16_t)b2;
+    }
+    __syncthreads();
+    const uint32_t total = P.loff[nsub];
+    for (uint32_t i = threadIdx.x; i < total; i += kPartThreads) {
+        const uint32_t b2 = P.sbk[i];
+        const uint32_t idx = P.base[b2] + (i - P.loff[b2]);
+        if (idx < (uint32_t)kBucket) s.ent2[((size_t)(bb + b2) << kBucketLog) + idx] = P.stage[i];
+        else bad = 1;
+    }
+    if (bad) report(s, kErrInput);
+}
+
+// One bucket of kBucket positions per CTA: lengths scattered into shared
+// memory by position, usefulness flags (K1), compaction (K2) and the
+// bucket's place in LLRc by look-back (K3).  Each warp owns a contiguous
+// range of 64 runs of 32 positions, so L_{k-1} comes from the lane to the
+// left (or the previous run's last lane).
+__global__ void __launch_bounds__(kBucketThreads)
+k_bucket_llr(int32_t n, Scratch s) {
+    constexpr int kChunks = kBucket / kWarp;                 // 1024 runs of 32 positions
+    constexpr int kWarps = kBucketThreads / kWarp;           // 16
+    constexpr int kRunsPerWarp = kChunks / kWarps;           // 64
+    constexpr int kTilesPerBucket = kBucket / kTile;         // 16
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint16_t* sL = reinterpret_cast<uint16_t*>(smem_raw);                        // kBucket lengths
+    unsigned* cmask = reinterpret_cast<unsigned*>(smem_raw + kBucket * 2);       // kChunks flag masks
+    int32_t* ccnt = reinterpret_cast<int32_t*>(cmask + kChunks);                 // kChunks run offsets
+    __shared__ int32_t wsum[kWarps];
+    __shared__ long long b_s, base_s;
+    __shared__ int32_t total_s;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) b_s = atomicAdd(&s.tickets[1], 1u);
+    for (int i = tid; i < kChunks; i += kBucketThreads) cmask[i] = 0;
+    __syncthreads();
+    const long long b = b_s;
+    const long long k0 = b * kBucket;
+    const int cnt = (int)(((long long)n - k0 < kBucket) ? (long long)n - k0 : kBucket);
+
+    // scatter the bucket's lengths into shared memory by position; cmask
+    // serves as a bitmap of the positions seen, so that a position given
+    // twice (sa not a permutation) is caught
+    const uint32_t* ent = s.ent2 + ((size_t)b << kBucketLog);
+    const uint32_t fill = __ldcg(s.cursor2 + (size_t)b * kCursorStride);
+    unsigned bad = fill != (uint32_t)cnt;
+    const int nent = (int)(fill < (uint32_t)cnt ? fill : (uint32_t)cnt);
+    for (int i = tid; i < nent; i += kBucketThreads) {
+        const uint32_t e = __ldcs(ent + i);
+        const uint32_t low = e >> 17, f = e & kEsc17;
+        if (low < (uint32_t)cnt) {
+            sL[low] = (uint16_t)(f == kEsc17 ? 0xffffu : f);
+            const unsigned bit = 1u << (low & 31);
+            if (atomicOr(cmask + (low >> 5), bit) & bit) bad = 1;
+        } else {
+            bad = 1;
+        }
+    }
+    if (bad) report(s, kErrInput);
+    __syncthreads();
+    auto len_at = [&](int x) -> int32_t {                    // L of position k0 + x, 0 <= x < cnt
+        const uint32_t f = sL[x];
+        return f == 0xffffu ? __ldcg(s.lbig + k0 + x) : (int32_t)f;
+    };
+
+    // K1 flags, one ballot per run, runs of a warp contiguous
+    int32_t left = 0;                                        // L of the position before the run
+    {
+        const int x0 = warp * kRunsPerWarp * kWarp;
+        left = (x0 == 0) ? ((k0 > 0) ? __ldcg(s.halo + b) : 0) : (x0 - 1 < cnt ? len_at(x0 - 1) : 0);
+    }
+    __syncthreads();                                         // cmask is rewritten below
+    for (int r = 0; r < kRunsPerWarp; ++r) {
+        const int c = warp * kRunsPerWarp + r;
+        const int x = c * kWarp + lane;
+        const int32_t L = (x < cnt) ? len_at(x) : 0;
+        int32_t prev = __shfl_up_sync(kFull, L, 1);
+        if (lane == 0) prev = left;
+        left = __shfl_sync(kFull, L, kWarp - 1);
+        const unsigned m = __ballot_sync(kFull, x < cnt && L > 0 && L >= prev);
+        if (lane == 0) { cmask[c] = m; ccnt[c] = __popc(m); }
+    }
+    __syncthreads();
+    // exclusive scan of the 1024 run counts: 2 per thread
+    {
+        const int a0 = ccnt[2 * tid], a1 = ccnt[2 * tid + 1];
+        const int incl = warp_incl_scan(a0 + a1);
+        if (lane == kWarp - 1) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = (lane < kWarps) ? wsum[lane] : 0;
+            const int wi = warp_incl_scan(v);
+            if (lane < kWarps) wsum[lane] = wi - v;
+            if (lane == kWarp - 1) total_s = wi;
+        }
+        __syncthreads();
+        const int ex = wsum[warp] + incl - a0 - a1;
+        ccnt[2 * tid] = ex;
+        ccnt[2 * tid + 1] = ex + a0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const long long ex = lookback_exclusive(s.status_b, b, total_s, s.err, s.qerr);
+        if (lane == 0) base_s = ex;
+    }
+    __syncthreads();
+    const long long base = base_s;
+    // first LLRc entry of each tile of the bucket
+    if (tid < kTilesPerBucket) {
+        const long long tile = b * kTilesPerBucket + tid;
+        if (tile < s.ntiles) s.tile_cbase[tile] = (int32_t)(base + ccnt[tid * (kTile / kWarp)]);
+        if (tile == s.ntiles - 1) s.tile_cbase[s.ntiles] = (int32_t)(base + total_s);
+    }
+    // K3: write the kept LLR's
+    for (int r = 0; r < kRunsPerWarp; ++r) {
+        const int c = warp * kRunsPerWarp + r;
+        const unsigned m = cmask[c];
+        if ((m >> lane) & 1u) {
+            const int x = c * kWarp + lane;
+            const long long o = base + ccnt[c] + __popc(m & ((1u << lane) - 1u));
+            s.cstart[o] = (int32_t)(k0 + x);
+            s.cend[o] = (int32_t)(k0 + x + len_at(x) - 1);
+        }
+    }
+}
+
+size_t bucket_smem_bytes() { return (size_t)kBucket * 2 + (size_t)(kBucket / kWarp) * 8; }
+
+void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream) {
+    const unsigned g1 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
+    k_part1<<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s);
+    const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
+    k_part2<<<g2, kPartThreads, part_smem_bytes(kSubPerSuper), stream>>>(n, s);
+}
+
+void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream) {
+    k_bucket_llr<<<(unsigned)s.nbuckets, kBucketThreads, bucket_smem_bytes(), stream>>>(n, s);
+}
+
+cudaError_t configure_front() {
+    cudaError_t e = cudaFuncSetAttribute(k_bucket_llr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bucket_smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_part1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_part2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)part_smem_bytes(kSubPerSuper));
+}
+
+}  // namespace lr

@@ -6,29 +6,54 @@
 
 namespace lr {
 
-constexpr int kTile = 2048;        // positions per tile (one CTA)
-constexpr int kThreads = 256;      // threads per CTA
-constexpr int kCoverCap = 4096;    // compact LLR's a tile stages in shared memory
+// Tiles of the gather front end and of the cover kernel.
+constexpr int kTile = 2048;          // positions per tile (one CTA)
+constexpr int kThreads = 256;        // threads per tile CTA
+constexpr int kCoverCap = 4096;      // compact LLR's a cover tile stages in shared memory
+
+// Rank-order front end: a two-level radix partition of <position, L> by the
+// position, into super-buckets of 2^20 and then buckets of 2^16 positions.
+constexpr int kSuperLog = 20;
+constexpr int kSuper = 1 << kSuperLog;         // positions per super-bucket
+constexpr int kBucketLog = 15;
+constexpr int kBucket = 1 << kBucketLog;       // positions per bucket (one bucket CTA)
+constexpr int kSubPerSuper = kSuper / kBucket; // 32
+constexpr int kBucketThreads = 512;            // threads of the bucket CTA
+constexpr int kPartThreads = 1024;             // threads of a partition CTA
+constexpr int kPartPer = 8;                    // entries per thread per partition CTA
+constexpr int kPartRound = kPartThreads * kPartPer;   // 8192 entries per partition CTA
+constexpr uint32_t kEsc12 = 0xfffu;            // 12-bit length field of level 1: value in lbig
+constexpr uint32_t kEsc17 = 0x1ffffu;          // 17-bit length field of level 2: value in lbig
+constexpr int kCursorStride = 32;              // one 128-byte line per partition cursor
 
 // Device scratch of one query, carved out of one allocation by the context.
-struct TileScratch {
-    unsigned* tickets;             // [0] ticket of k_llr_compact, [1] of k_cover
+struct Scratch {
+    unsigned* tickets;             // [0] gather tiles, [1] buckets, [2] cover tiles
     unsigned* qerr;                // error bits of this query (cleared with the tickets)
     unsigned* err;                 // sticky device error bits (kErr*), read by the host
-    unsigned long long* status_c;  // per-tile look-back words, LLRc counts
-    unsigned long long* status_o;  // per-tile look-back words, LR counts
-    int32_t* cbase;                // ntiles + 1: compact LLR's starting before tile j
+    unsigned long long* status_g;  // look-back words of the gather front end (per tile)
+    unsigned long long* status_b;  // look-back words of the rank-order front end (per bucket)
+    unsigned long long* status_o;  // look-back words of the cover kernel (per tile)
+    int32_t* tile_cbase;           // ntiles + 1: compact LLR's starting before tile j
     int32_t* cstart;               // n: compact LLR starts (ascending)
     int32_t* cend;                 // n: compact LLR ends   (ascending)
+    uint32_t* ent1;                // nsupers x 2^20: level-1 entries <pos mod 2^20, min(L, 4095)>
+    uint32_t* ent2;                // nbuckets x 2^15: level-2 entries <pos mod 2^15, min(L, 2^17-1)>
+    unsigned* cursor1;             // fill counts of ent1, one per kCursorStride words (cleared per query)
+    unsigned* cursor2;             // fill counts of ent2, one per kCursorStride words (cleared per query)
+    int32_t* lbig;                 // n: L of positions whose length field escaped
+    int32_t* halo;                 // nbuckets + 1: L of the position before each bucket
     long long ntiles;
-    void* zero_base;               // tickets + status words, cleared before every query
+    long long nbuckets;
+    long long nsupers;
+    void* zero_base;               // tickets, status words and cursors, cleared before every query
     size_t zero_bytes;
 };
 
 inline long long num_tiles(long long n) { return (n + kTile - 1) / kTile; }
+inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
+inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
 
-cudaError_t configure_kernels();
-size_t cover_smem_bytes();
 constexpr int kMaxPhases = 8;
 
 // Optional per-kernel events: ev[i] is recorded before kernel i and
@@ -36,11 +61,22 @@ constexpr int kMaxPhases = 8;
 struct PhaseEvents {
     cudaEvent_t ev[kMaxPhases + 1];
     bool enabled = false;
+    int count = 0;                 // phases recorded by the last query
 };
 
-cudaError_t launch_query(const int32_t* rank, const int32_t* lcp, int32_t n, const TileScratch& s,
+// Launches the whole query on `stream`: the front end (rank-order when sa is
+// non-null, else the rank gather) and the cover kernel.
+cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
                          int32_t* lr_len, int32_t* lr_start, int64_t* offsets, int32_t* starts,
                          long long capacity, bool all, cudaStream_t stream, int* launches,
                          PhaseEvents* events);
+
+// Front ends (lr_front.cu) and the cover kernel (lr_cover.cu).
+void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream);
+void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream);
+void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream);
+void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
+                  int32_t* starts, long long capacity, bool all, cudaStream_t stream);
+cudaError_t configure_kernels();
 
 }  // namespace lr

@@ -50,7 +50,7 @@ def test_argument_errors_need_no_gpu(lib_path):
     assert lib.lr_create(None, 0) == lr.LR_ERR_ARG
     assert lib.lr_create(ctypes.byref(h), -1) == lr.LR_ERR_ARG
     null = ctypes.c_void_p(0)
-    assert lib.lr_query_all(null, null, null, null, 5, null, null, null, null, 0, None) == lr.LR_ERR_ARG
+    assert lib.lr_query_all(null, null, null, null, null, 5, null, null, null, null, 0, None) == lr.LR_ERR_ARG
     assert lib.lr_destroy(null) == lr.LR_ERR_ARG
 
 

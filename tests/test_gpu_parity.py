@@ -33,8 +33,14 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _gpu_all(ctx, rank, lcp):
-    out = ctx.query_all(_dev(rank), _dev(lcp))
+FRONTS = ("sa", "rank")        # rank-order front end (suffix array given) and the rank gather
+
+
+def _gpu_all(ctx, sa, rank, lcp, front="sa"):
+    if front == "sa":
+        out = ctx.query_all(_dev(lcp), sa=_dev(sa))
+    else:
+        out = ctx.query_all(_dev(lcp), rank=_dev(rank))
     return tuple(t.cpu().numpy() for t in out)
 
 
@@ -50,10 +56,12 @@ def _assert_csr_equal(got, want, what=""):
 def _full_check(ctx, text):
     sa, rank, lcp = W.prep(text)
     want = oracle.lr_all_raw(rank, lcp)
-    got = _gpu_all(ctx, rank, lcp)
-    _assert_csr_equal(got, want, "n=%d" % text.size)
-    st, ln = ctx.query_leftmost(_dev(rank), _dev(lcp))
-    assert np.array_equal(st.cpu().numpy(), want[1]) and np.array_equal(ln.cpu().numpy(), want[0])
+    for front in FRONTS:
+        got = _gpu_all(ctx, sa, rank, lcp, front)
+        _assert_csr_equal(got, want, "n=%d front=%s" % (text.size, front))
+        kw = {"sa": _dev(sa)} if front == "sa" else {"rank": _dev(rank)}
+        st, ln = ctx.query_leftmost(_dev(lcp), **kw)
+        assert np.array_equal(st.cpu().numpy(), want[1]) and np.array_equal(ln.cpu().numpy(), want[0])
 
 
 def _sampled_check(ctx, w, got, nsamples, seed):
@@ -125,37 +133,58 @@ def test_wide_windows_spill_to_global(ctx):
         parts.append(np.array([ord("#")], np.uint8))
     text = np.concatenate(parts)
     w = W.Workload("wide", text, *W.prep(text))
-    got = _gpu_all(ctx, w.rank, w.lcp)
-    _sampled_check(ctx, w, got, 3000, 5)
     ks = np.arange(Wn - 50, Wn + 50)
     wl, ws, wo, wst = oracle.lr_at(w.rank, w.lcp, ks)
-    assert int(np.diff(wo).max()) >= 1
-    for q, k in enumerate(ks):
-        assert np.array_equal(got[3][got[2][k]:got[2][k + 1]], wst[wo[q]:wo[q + 1]])
+    assert int(np.diff(wo).max()) > 4096                      # wider than the staged window
+    for front in FRONTS:
+        got = _gpu_all(ctx, w.sa, w.rank, w.lcp, front)
+        _sampled_check(ctx, w, got, 3000, 5)
+        for q, k in enumerate(ks):
+            assert np.array_equal(got[3][got[2][k]:got[2][k + 1]], wst[wo[q]:wo[q + 1]])
 
 
 # ------------------------------------------------------------------ workloads
 
-def test_dna_iid_1m_full(ctx):
+@pytest.mark.parametrize("front", FRONTS)
+def test_dna_iid_1m_full(ctx, front):
     w = W.single("dna_iid_1m")
-    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+    _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp), w.name)
 
 
-def test_dna_planted_4m_full(ctx):
+@pytest.mark.parametrize("front", FRONTS)
+def test_dna_planted_4m_full(ctx, front):
     w = W.single("dna_64m", n=4 * W.MI)
-    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+    _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp), w.name)
 
 
-def test_english_4m_full(ctx):
+@pytest.mark.parametrize("front", FRONTS)
+def test_english_4m_full(ctx, front):
     w = W.single("english_256m", n=4 * W.MI)
-    _assert_csr_equal(_gpu_all(ctx, w.rank, w.lcp), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+    _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp), w.name)
+
+
+def test_multi_bucket_sizes(ctx):
+    """Sizes around the 65536-position buckets of the rank-order front end."""
+    for n in (65535, 65536, 65537, 3 * 65536 + 1):
+        _full_check(ctx, W.make_text("dna", n, 11))
+
+
+def test_long_lengths_escape_16_bits(ctx):
+    """LLR lengths >= 65535 take the escape path of the packed partition entries."""
+    rng = np.random.default_rng(12)
+    base = rng.integers(65, 69, 300_000).astype(np.uint8)
+    base[200_000:280_000] = base[20_000:100_000]                  # an 80k exact copy
+    _full_check(ctx, base)
 
 
 @pytest.mark.parametrize("name", ["dna_64m", "english_256m"])
 def test_full_size_sampled(ctx, name):
     w = W.single(name)
-    got = _gpu_all(ctx, w.rank, w.lcp)
+    got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa")
     _sampled_check(ctx, w, got, 4000, 17)
+    got2 = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
+    for a, b in zip(got, got2):
+        assert np.array_equal(a, b)
 
 
 # ------------------------------------------------------------------ API behaviour
@@ -163,13 +192,13 @@ def test_full_size_sampled(ctx, name):
 def test_capacity_error_keeps_offsets(ctx):
     w = W.single("dna_64m", n=100_000)
     want = oracle.lr_all_raw(w.rank, w.lcp)
-    rank, lcp = _dev(w.rank), _dev(w.lcp)
+    sa, lcp = _dev(w.sa), _dev(w.lcp)
     n = w.n
     ln = torch.empty(n, dtype=torch.int32, device="cuda")
     st = torch.empty(n, dtype=torch.int32, device="cuda")
     off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
     small = torch.full((1000,), -7, dtype=torch.int32, device="cuda")
-    status, total = P.lr_query_all(ctx.handle, rank, lcp, ln, st, off, small)
+    status, total = P.lr_query_all(ctx.handle, sa, None, lcp, ln, st, off, small)
     assert status == P.LR_ERR_CAPACITY and total == want[3].size
     assert np.array_equal(off.cpu().numpy(), want[2]) and np.array_equal(ln.cpu().numpy(), want[0])
     assert np.array_equal(small.cpu().numpy(), want[3][:1000])
@@ -183,9 +212,10 @@ def test_host_buffer_entry_point(ctx):
     st = np.empty(n, np.int32)
     off = np.empty(n + 1, np.int64)
     starts = np.empty(2 * n, np.int32)
-    status, total = P.lr_query_all_host(ctx.handle, w.rank, w.lcp, ln, st, off, starts)
-    assert status == P.LR_OK
-    _assert_csr_equal((ln, st, off, starts[:total]), want, "host")
+    for sa, rank in ((w.sa, None), (None, w.rank)):
+        status, total = P.lr_query_all_host(ctx.handle, sa, rank, w.lcp, ln, st, off, starts)
+        assert status == P.LR_OK
+        _assert_csr_equal((ln, st, off, starts[:total]), want, "host")
 
 
 def test_invalid_arguments(ctx):
@@ -195,49 +225,59 @@ def test_invalid_arguments(ctx):
     null = ctypes.c_void_p(0)
     tot = ctypes.c_int64()
     s = P._stream(None)
+    T = P._ptr(t)
     for n in (0, -5, 2**31 - 1):
-        assert lib.lr_query_all(ctx.handle, s, P._ptr(t), P._ptr(t), n, P._ptr(t), P._ptr(t), P._ptr(t),
-                                P._ptr(t), 4, ctypes.byref(tot)) == P.LR_ERR_ARG
-    assert lib.lr_query_all(ctx.handle, s, null, P._ptr(t), 3, P._ptr(t), P._ptr(t), P._ptr(t),
-                            P._ptr(t), 4, ctypes.byref(tot)) == P.LR_ERR_ARG
-    assert lib.lr_query_leftmost(ctx.handle, s, P._ptr(t), null, 3, P._ptr(t), P._ptr(t)) == P.LR_ERR_ARG
+        assert lib.lr_query_all(ctx.handle, s, T, null, T, n, T, T, T, T, 4, ctypes.byref(tot)) == P.LR_ERR_ARG
+    assert lib.lr_query_all(ctx.handle, s, null, null, T, 3, T, T, T, T, 4, ctypes.byref(tot)) == P.LR_ERR_ARG
+    assert lib.lr_query_leftmost(ctx.handle, s, null, T, null, 3, T, T) == P.LR_ERR_ARG
 
 
 def test_bad_sentinel_and_rank_are_reported(ctx):
     w = W.single("dna_iid_1m", n=5000)
     lcp = w.lcp.copy()
     lcp[0] = 3
-    with pytest.raises(P.LRError) as e:
-        ctx.query_all(_dev(w.rank), _dev(lcp))
-    assert e.value.status == P.LR_ERR_SENTINEL
+    for kw in ({"sa": _dev(w.sa)}, {"rank": _dev(w.rank)}):
+        with pytest.raises(P.LRError) as e:
+            ctx.query_all(_dev(lcp), **kw)
+        assert e.value.status == P.LR_ERR_SENTINEL
     rank = w.rank.copy()
-    rank[17] = w.n + 100                                                   # out of range: clamped, reported
+    rank[17] = w.n + 100                                       # out of range: clamped, reported
     with pytest.raises(P.LRError) as e:
-        ctx.query_all(_dev(rank), _dev(w.lcp))
+        ctx.query_all(_dev(w.lcp), rank=_dev(rank))
+    assert e.value.status == P.LR_ERR_SENTINEL
+    sa = w.sa.copy()
+    sa[17] = sa[18]                                            # not a permutation: detected, reported
+    with pytest.raises(P.LRError) as e:
+        ctx.query_all(_dev(w.lcp), sa=_dev(sa))
+    assert e.value.status == P.LR_ERR_SENTINEL
+    sa[17] = -4                                                # out of range
+    with pytest.raises(P.LRError) as e:
+        ctx.query_all(_dev(w.lcp), sa=_dev(sa))
     assert e.value.status == P.LR_ERR_SENTINEL
     # the context stays usable
-    got = _gpu_all(ctx, w.rank, w.lcp)
-    _assert_csr_equal(got, oracle.lr_all_raw(w.rank, w.lcp))
+    for front in FRONTS:
+        _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp))
 
 
 def test_maximum_size_closed_form(ctx):
     """S = a^n with n = 2^31 - 2, the largest n the ABI takes.
 
-    sa[r] = n-1-r, rank[i] = n-1-i, lcp = [0, 1, ..., n-1, 0]; so L_0 = n-1,
-    L_i = n-i, only <0, n-1> and <1, n-1> are useful, and LR_k is {0} for
+    sa[r] = n-1-r, rank[i] = n-1-i, lcp = [0, 1, ..., n-1, 0]; so L_0 = n-1
+    and L_i = n-i (all beyond the 16-bit length field of the partition
+    entries), only <0, n-1> and <1, n-1> are useful, and LR_k is {0} for
     k = 0, {0, 1} for 0 < k < n-1 and {1} for k = n-1, all of length n-1.
     The total (2n - 2) exceeds 2^31, exercising the int64 offsets.
     """
     free, _ = torch.cuda.mem_get_info()
     n = 2**31 - 2
-    need = n * (4 + 4 + 4 + 4 + 8 + 8 + 8) + (1 << 30)
+    need = n * (4 + 4 + 4 + 4 + 8 + 8 + 16 + 8) + (1 << 30)
     if free < need:
         pytest.skip("needs %.0f GB free" % (need / 1e9))
-    rank = torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda")
+    sa = torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda")     # rank is the same array
     lcp = torch.arange(0, n + 1, dtype=torch.int32, device="cuda")
     lcp[n] = 0
-    ln, st, off, starts = ctx.query_all(rank, lcp, capacity=2 * n)
-    del rank, lcp
+    ln, st, off, starts = ctx.query_all(lcp, sa=sa, capacity=2 * n)
+    del sa, lcp
     assert int(off[n]) == 2 * n - 2
     assert bool((ln == n - 1).all())
     assert bool((st[:n - 1] == 0).all()) and int(st[n - 1]) == 1
