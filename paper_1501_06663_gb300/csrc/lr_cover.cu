@@ -4,8 +4,8 @@
 //
 // Starts and ends of LLRc strictly increase (Sec. 3.2), so the compact LLR's
 // covering a position k form a contiguous window of LLRc whose two ends only
-// move right as k grows.  Per tile of kTile positions (tiles in order by an
-// atomic ticket):
+// move right as k grows.  Per tile of kCoverTile positions (tiles in order
+// by an atomic ticket):
 //
 //  * the window range of the whole tile is LLRc[lo, cb1): the tile's own
 //    entries [cb0, cb1) plus the carry [lo, cb0), the earlier entries whose
@@ -33,8 +33,8 @@ namespace lr {
 
 namespace {
 
-constexpr int kWarps = kThreads / kWarp;          // 8
-constexpr int kChunks = kTile / kWarp;             // 64 runs of 32 positions
+constexpr int kWarps = kCoverThreads / kWarp;     // 16
+constexpr int kChunks = kCoverTile / kWarp;        // 128 runs of 32 positions
 constexpr int kChunksPerWarp = kChunks / kWarps;   // 8
 
 struct __align__(16) CoverSmem {
@@ -48,20 +48,43 @@ struct __align__(16) CoverSmem {
     long long tile;
     long long obase;
     int32_t lo;
+    int32_t ttot;                    // the tile's total of tie counts
 };
 
-__device__ __forceinline__ void popc_prefix64(const unsigned* map, int32_t* pre) {
+// Exclusive prefix popcounts of the kChunks bitmap words, by one warp.
+__device__ __forceinline__ void popc_prefix(const unsigned* map, int32_t* pre) {
+    constexpr int kPer = kChunks / kWarp;
     const int lane = lane_id();
-    const int a = __popc(map[2 * lane]), b = __popc(map[2 * lane + 1]);
-    const int incl = warp_incl_scan(a + b);
-    pre[2 * lane] = incl - a - b;
-    pre[2 * lane + 1] = incl - b;
+    int c[kPer], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) { c[i] = __popc(map[kPer * lane + i]); sum += c[i]; }
+    int run = warp_incl_scan(sum) - sum;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) { pre[kPer * lane + i] = run; run += c[i]; }
+}
+
+// Exclusive scan of the kChunks ints of a[] by one warp; returns the total.
+__device__ __forceinline__ int scan_chunks(int32_t* a) {
+    constexpr int kPer = kChunks / kWarp;
+    const int lane = lane_id();
+    int c[kPer], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) { c[i] = a[kPer * lane + i]; sum += c[i]; }
+    const int incl = warp_incl_scan(sum);
+    int run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) { a[kPer * lane + i] = run; run += c[i]; }
+    return __shfl_sync(kFull, incl, kWarp - 1);
 }
 
 }  // namespace
 
+#ifndef LR_COVER_MIN_BLOCKS
+#define LR_COVER_MIN_BLOCKS 3
+#endif
+
 template <bool kAll>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kCoverThreads, LR_COVER_MIN_BLOCKS)
 k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict__ lr_start,
         int64_t* __restrict__ offsets, int32_t* __restrict__ starts, long long capacity) {
     __shared__ CoverSmem sm;
@@ -70,93 +93,179 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
     __syncthreads();
     const long long tile = sm.tile;
-    const int32_t k0 = (int32_t)(tile * kTile);              // n < 2^31: positions fit 32 bits
+    const int32_t k0 = (int32_t)(tile * kCoverTile);         // n < 2^31: positions fit 32 bits
     // LLRc entries [cb0, cb1) start inside this tile; clamped so that a
     // corrupted front end (already reported) cannot send reads out of bounds
-    int32_t cb0 = s.tile_cbase[tile], cb1 = s.tile_cbase[tile + 1];
+    const long long ft = tile * kCoverTilesPer;               // first front-end tile
+    const long long ft1 = (ft + kCoverTilesPer < s.ntiles) ? ft + kCoverTilesPer : s.ntiles;
+    int32_t cb0 = s.tile_cbase[ft], cb1 = s.tile_cbase[ft1];
     cb0 = cb0 < 0 ? 0 : (cb0 > n ? n : cb0);
     cb1 = cb1 < cb0 ? cb0 : (cb1 > n ? n : cb1);
 
-    // carry: entries before cb0 whose end reaches k0 (a suffix, ends increase)
+    // Stage LLRc[cb0 - kSpec, cb1): the tile's own entries and, in the same
+    // round trip, the kSpec entries before them, which hold the carry (the
+    // entries whose end reaches k0: a suffix, ends increase) unless it is
+    // longer than kSpec.  A longer carry takes the slow path below.
+    constexpr int32_t kSpec = 64;
+    const int32_t sbase = cb0 > kSpec ? cb0 - kSpec : 0;
+    const int32_t MS = cb1 - sbase;
+    const bool fits = MS <= kCoverCap;
+    if (fits) {
+        for (int i = tid; i < MS; i += kCoverThreads) {
+            const int32_t cs = __ldg(s.cstart + sbase + i), ce = __ldg(s.cend + sbase + i);
+            sm.cs[i] = cs; sm.cl[i] = ce;                        // ends for now, lengths below
+        }
+    }
+    __syncthreads();
     if (warp == 0) {
         int32_t t = cb0;
-        while (t > 0) {
-            const int32_t idx = t - 1 - lane;
-            const bool reach = idx >= 0 && __ldg(s.cend + idx) >= k0;
-            const unsigned m = __ballot_sync(kFull, reach);
-            if (m == kFull) { t -= kWarp; continue; }
-            t -= __ffs(~m) - 1;
-            break;
+        bool done = false;
+        if (fits) {                                              // scan the staged speculative part
+            while (t > sbase) {
+                const int32_t idx = t - 1 - lane;
+                const bool reach = idx >= sbase && sm.cl[idx - sbase] >= k0;
+                const unsigned m = __ballot_sync(kFull, reach);
+                if (m == kFull) { t -= kWarp; continue; }
+                t -= __ffs(~m) - 1;
+                done = true;
+                break;
+            }
+            if (t == 0) done = true;
+        }
+        if (!done) {                                             // carry longer than staged: scan LLRc
+            while (t > 0) {
+                const int32_t idx = t - 1 - lane;
+                const bool reach = idx >= 0 && __ldg(s.cend + idx) >= k0;
+                const unsigned m = __ballot_sync(kFull, reach);
+                if (m == kFull) { t -= kWarp; continue; }
+                t -= __ffs(~m) - 1;
+                break;
+            }
         }
         if (lane == 0) sm.lo = t;
     }
     __syncthreads();
     const int32_t lo = sm.lo;
     const int32_t C = cb0 - lo, M = cb1 - lo;
-    const bool staged = M <= kCoverCap;
-    for (int i = tid; i < M; i += kThreads) {
-        const int32_t cs = __ldg(s.cstart + lo + i), ce = __ldg(s.cend + lo + i);
-        if (staged) { sm.cs[i] = cs; sm.cl[i] = ce - cs + 1; }
-        const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
-        if (i >= C && xs < (uint32_t)kTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
-        if (xe < (uint32_t)kTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
+    // staged: window entry v sits at sm.cs/cl[v + shift]
+    const bool staged = fits && lo >= sbase;
+    const int32_t shift = staged ? lo - sbase : 0;
+    if (staged) {
+        for (int i = tid; i < M; i += kCoverThreads) {
+            const int32_t cs = sm.cs[shift + i], ce = sm.cl[shift + i];
+            sm.cl[shift + i] = ce - cs + 1;
+            const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
+            if (i >= C && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
+            if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
+        }
+    } else {
+        for (int i = tid; i < M; i += kCoverThreads) {
+            const int32_t cs = __ldg(s.cstart + lo + i), ce = __ldg(s.cend + lo + i);
+            const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
+            if (i >= C && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
+            if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
+        }
     }
     __syncthreads();
-    if (warp == 0) popc_prefix64(sm.smap, sm.spre);
-    if (warp == 1) popc_prefix64(sm.emap, sm.epre);
+    if (warp == 0) popc_prefix(sm.smap, sm.spre);
+    if (warp == 1) popc_prefix(sm.emap, sm.epre);
     __syncthreads();
 
     // candidate v of the range: start and length (shared memory, or LLRc in
     // place when the range is too long to stage)
     const int32_t* gcs = s.cstart + lo;
     const int32_t* gce = s.cend + lo;
-    auto start_of = [&](int32_t v) -> int32_t { return staged ? sm.cs[v] : __ldg(gcs + v); };
-    auto len_of = [&](int32_t v) -> int32_t { return staged ? sm.cl[v] : __ldg(gce + v) - __ldg(gcs + v) + 1; };
+    const int32_t* SCS = sm.cs + shift;
+    const int32_t* SCL = sm.cl + shift;
+    auto start_of = [&](int32_t v) -> int32_t { return staged ? SCS[v] : __ldg(gcs + v); };
     const unsigned below = (1u << lane) - 1u;
     // window [lw, hi] of this lane's position in run c (carry ++ local numbering)
     auto window = [&](int c, int32_t& lw, int32_t& hi) {
         hi = C + sm.spre[c] + __popc(sm.smap[c] & (below | (1u << lane))) - 1;
         lw = sm.epre[c] + __popc(sm.emap[c] & below);
     };
+    // longest length b over the window, index vb of its leftmost holder and
+    // the number of holders ct: the first four entries without branches
+    // (nearly every window), a loop for the rest
+    auto best_of = [&](int32_t lw, int32_t hi, int32_t& b, int32_t& vb, int32_t& ct) {
+        b = 0; vb = -1; ct = 0;
+        auto step = [&](int32_t len, int32_t v) {
+            const bool gt = len > b;
+            ct = gt ? 1 : ct + (len == b);
+            vb = gt ? v : vb;
+            b = gt ? len : b;
+        };
+        if (staged) {
+            const int32_t* CL = SCL;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t v = lw + u;
+                const int32_t len = (v <= hi) ? CL[v] : -1;
+                step(len, v);
+            }
+            for (int32_t v = lw + 4; v <= hi; ++v) step(CL[v], v);
+        } else {
+            for (int32_t v = lw; v <= hi; ++v) step(__ldg(gce + v) - __ldg(gcs + v) + 1, v);
+        }
+    };
     // per run: longest length, index of its leftmost holder, number of ties
     int32_t best[kChunksPerWarp], vbest[kChunksPerWarp], cnt[kChunksPerWarp];
 #pragma unroll
     for (int q = 0; q < kChunksPerWarp; ++q) {
         const int c = q * kWarps + warp;
-        const int32_t k = k0 + c * kWarp + lane;
-        int32_t lw, hi;
+        int32_t lw, hi, b, vb, ct;
         window(c, lw, hi);
-        int32_t b = 0, vb = -1, ct = 0;
-        for (int32_t v = lw; v <= hi; ++v) {
-            const int32_t len = len_of(v);
-            if (len > b) { b = len; vb = v; ct = 1; }
-            else if (len == b) ++ct;
-        }
+        best_of(lw, hi, b, vb, ct);
         best[q] = b; vbest[q] = vb; cnt[q] = ct;
-        if (k < n) { __stcs(lr_len + k, b); __stcs(lr_start + k, vb >= 0 ? start_of(vb) : -1); }
     }
-
+    int pre[kChunksPerWarp];
     if constexpr (kAll) {
-        // CSR offsets: scan of the tie counts within the tile, then the
-        // tile's base by look-back over the tiles' totals
-        int pre[kChunksPerWarp];
+        // CSR offsets: scan of the tie counts within the tile.  Counts are
+        // almost always 0, 1 or 2: the run scan is then three ballots.  The
+        // tile's total is published before the per-position stores, so that
+        // later tiles rarely wait for it.
 #pragma unroll
         for (int q = 0; q < kChunksPerWarp; ++q) {
-            const int incl = warp_incl_scan(cnt[q]);
+            int incl;
+            if (__any_sync(kFull, cnt[q] > 3)) {
+                incl = warp_incl_scan(cnt[q]);
+            } else {
+                const unsigned upto = below | (1u << lane);
+                incl = __popc(__ballot_sync(kFull, cnt[q] >= 1) & upto) +
+                       __popc(__ballot_sync(kFull, cnt[q] >= 2) & upto) +
+                       __popc(__ballot_sync(kFull, cnt[q] >= 3) & upto);
+            }
             pre[q] = incl - cnt[q];
             if (lane == kWarp - 1) sm.chunk[q * kWarps + warp] = incl;
         }
         __syncthreads();
         if (warp == 0) {
-            const int x = sm.chunk[2 * lane], y = sm.chunk[2 * lane + 1];
-            const int incl = warp_incl_scan(x + y);
-            sm.chunk[2 * lane] = incl - x - y;
-            sm.chunk[2 * lane + 1] = incl - y;
-            const int tot = __shfl_sync(kFull, incl, kWarp - 1);
-            const long long ex = lookback_exclusive(s.status_o, tile, tot, s.err, s.qerr);
+            const int tot = scan_chunks(sm.chunk);
             if (lane == 0) {
+                publish(s.status_o, tile, tile == 0 ? kPrefix : kAggregate, tot);
+                sm.ttot = tot;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kChunksPerWarp; ++q) {
+        const int c = q * kWarps + warp;
+        const int32_t k = k0 + c * kWarp + lane;
+        if (k < n) {
+            __stcs(lr_len + k, best[q]);
+            __stcs(lr_start + k, vbest[q] >= 0 ? start_of(vbest[q]) : -1);
+        }
+    }
+
+    if constexpr (kAll) {
+        __syncthreads();
+        if (warp == 0) {
+            const int tot = sm.ttot;
+            const long long ex = (tile == 0) ? 0 : lookback(s.status_o, tile, s.err, s.qerr);
+            if (lane == 0) {
+                if (tile != 0) publish(s.status_o, tile, kPrefix, ex + tot);
                 sm.obase = ex;
-                if (tile == s.ntiles - 1) offsets[n] = ex + tot;
+                if (tile == num_cover_tiles(n) - 1) offsets[n] = ex + tot;
             }
         }
         __syncthreads();
@@ -172,12 +281,13 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             // compact LLR of the longest length, ascending; with one holder
             // (the common case) it is already known
             if (o < capacity) __stcs(starts + o, start_of(vbest[q]));
-            ++o;
             if (cnt[q] > 1) {
+                ++o;
                 int32_t lw, hi;
                 window(c, lw, hi);
                 for (int32_t v = vbest[q] + 1; v <= hi; ++v) {
-                    if (len_of(v) == best[q]) {
+                    const int32_t len = staged ? SCL[v] : __ldg(gce + v) - __ldg(gcs + v) + 1;
+                    if (len == best[q]) {
                         if (o < capacity) __stcs(starts + o, start_of(v));
                         ++o;
                     }
@@ -189,11 +299,11 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
 
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
                   int32_t* starts, long long capacity, bool all, cudaStream_t stream) {
-    const unsigned grid = (unsigned)s.ntiles;
+    const unsigned grid = (unsigned)num_cover_tiles(n);
     if (all)
-        k_cover<true><<<grid, kThreads, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
+        k_cover<true><<<grid, kCoverThreads, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
     else
-        k_cover<false><<<grid, kThreads, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
+        k_cover<false><<<grid, kCoverThreads, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
 }
 
 }  // namespace lr

@@ -6,9 +6,16 @@
 
 namespace lr {
 
-// Tiles of the gather front end and of the cover kernel.
+// Tiles of the gather front end (and the granularity of tile_cbase).
 constexpr int kTile = 2048;          // positions per tile (one CTA)
 constexpr int kThreads = 256;        // threads per tile CTA
+// Tiles of the cover kernel: kCoverTilesPer front-end tiles each.
+#ifndef LR_COVER_TILES_PER
+#define LR_COVER_TILES_PER 2
+#endif
+constexpr int kCoverTilesPer = LR_COVER_TILES_PER;
+constexpr int kCoverTile = kTile * kCoverTilesPer;   // 4096 positions
+constexpr int kCoverThreads = kThreads * kCoverTilesPer;
 constexpr int kCoverCap = 4096;      // compact LLR's a cover tile stages in shared memory
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
@@ -33,7 +40,7 @@ struct Scratch {
     unsigned* err;                 // sticky device error bits (kErr*), read by the host
     unsigned long long* status_g;  // look-back words of the gather front end (per tile)
     unsigned long long* status_b;  // look-back words of the rank-order front end (per bucket)
-    unsigned long long* status_o;  // look-back words of the cover kernel (per tile)
+    unsigned long long* status_o;  // look-back words of the cover kernel (per cover tile)
     int32_t* tile_cbase;           // ntiles + 1: compact LLR's starting before tile j
     int32_t* cstart;               // n: compact LLR starts (ascending)
     int32_t* cend;                 // n: compact LLR ends   (ascending)
@@ -50,7 +57,8 @@ struct Scratch {
     size_t zero_bytes;
 };
 
-inline long long num_tiles(long long n) { return (n + kTile - 1) / kTile; }
+__host__ __device__ inline long long num_tiles(long long n) { return (n + kTile - 1) / kTile; }
+__host__ __device__ inline long long num_cover_tiles(long long n) { return (n + kCoverTile - 1) / kCoverTile; }
 inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
 inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
 
