@@ -133,6 +133,36 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
                             int64_t* h_total);
 
 /*
+ * lr_query_all_static -- lr_query_all for callers that cannot allocate.
+ *
+ * The paper has no counterpart of this entry point; it exists for library
+ * users who are not allowed to allocate device memory at query time: code
+ * that runs inside another framework's per-request callback (where a device
+ * allocation would synchronise the whole device and stall unrelated work),
+ * or services that fix their memory budget once at start-up.  It needs no
+ * context and allocates nothing: its working memory is one array of about
+ * 8 MB compiled into this library's device image, which every GPU that
+ * loads the library keeps until the process exits.
+ *
+ * Same inputs and outputs as lr_query_all with rank (the rank-gather front
+ * end), for 1 <= n <= LR_STATIC_MAX_N; larger n is rejected with
+ * LR_ERR_ARG (use lr_query_all).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array and leave their contents in it (the parts that must
+ * start at zero are cleared by every call), so calls on the same device
+ * must not overlap on the GPU: two streams running it at the same time
+ * race.  Errors of the kernels (bad input, a lost wait) are only reported
+ * when h_total is given, which makes the call wait for `stream`.
+ */
+#define LR_STATIC_MAX_N 1048576
+lr_status lr_query_all_static(lr_stream_t stream,
+                              const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                              int32_t* d_lr_len, int32_t* d_lr_start,
+                              int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
+                              int64_t* h_total);
+
+/*
  * Kernels launched by the most recent query of this context (for the
  * benchmark's launch accounting): 4 with sa, 2 with rank only.
  */

@@ -30,8 +30,11 @@ LR_ERR_BUSY = 7
 EXPORTED = (
     "lr_create", "lr_destroy", "lr_status_str", "lr_last_cuda_error", "lr_device_status",
     "lr_query_leftmost", "lr_query_all", "lr_query_all_host", "lr_last_launch_count",
-    "lr_set_phase_timing", "lr_phase_times", "lr_last_compact_size",
+    "lr_set_phase_timing", "lr_phase_times", "lr_last_compact_size", "lr_query_all_static",
 )
+
+#: largest n lr_query_all_static takes (LR_STATIC_MAX_N in include/lr.h)
+LR_STATIC_MAX_N = 1 << 20
 
 
 class LRError(RuntimeError):
@@ -65,6 +68,7 @@ def load(path: str | None = None):
     lib.lr_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
     lib.lr_phase_times.restype = i32
     lib.lr_last_compact_size.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    lib.lr_query_all_static.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -177,6 +181,20 @@ def lr_query_all_host(ctx, sa, rank, lcp, lr_len, lr_start, offsets, starts, str
     st = load().lr_query_all_host(ctx, _stream(stream), _ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(lr_len),
                                   _ptr(lr_start), _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot))
     return st, tot.value
+
+
+def lr_query_all_static(rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
+    """The all-LR query without any device allocation (no context; n <= LR_STATIC_MAX_N).
+
+    For callers that may not allocate at query time; see include/lr.h.  The
+    outputs are caller-provided device tensors.  Returns (status, total or None).
+    """
+    n = int(rank.numel())
+    cap = int(starts.numel()) if starts is not None else 0
+    tot = ctypes.c_int64(-1)
+    st = load().lr_query_all_static(_stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len), _ptr(lr_start),
+                                    _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot) if sync else None)
+    return st, (tot.value if sync else None)
 
 
 # ---------------------------------------------------------------- convenience
