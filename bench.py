@@ -117,25 +117,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
+def source_hash(files) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1501_06663_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(files):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernels are unchanged since."""
+def recorded_traffic(phase: str, workload: str, n: int):
+    """DRAM bytes per launch of a phase from the committed ncu summary, or
+    None if its kernel sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    ent = d.get("kernels", {}).get(kernel)
-    if not ent or ent.get("workload") != workload:
+    ent = json.load(open(p)).get("phases", {}).get(phase)
+    if not ent or ent.get("workload") != workload or ent.get("n") != n \
+            or ent.get("source_hash") != source_hash(ent["files"]):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -326,13 +324,13 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "parallelism": "replicas" if ws > 1 else "single",
-                       "inputs": "rank+lcp resident in HBM (%.2f GiB, larger than the 129 MB L2: no flush)"
+                       "inputs": "sa+lcp resident in HBM (%.2f GiB, larger than the 129 MB L2: no flush)"
                                  % ((8 * n + 4) / 2**30),
                        "input": "sa+lcp (rank-order front end)",
                        "total_lr_starts": total, "compact_llr": m},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "traffic": recorded_traffic(kname, args.workload),
+                         "traffic": recorded_traffic(kname, args.workload, n),
                          "algorithmic_bytes_per_launch": algo[kname], "avg_launch_ms": round(per[dom], 4)},
             "path_roofline": {"bound": "hbm", "achieved": round(path_achieved, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(path_achieved / peak, 4), "peak_kind": peak_kind,
