@@ -133,6 +133,73 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
                             int64_t* h_total);
 
 /*
+ * Batched query: many strings of uneven length in one set of launches over
+ * a flattened position space (the strings back to back).  String j owns the
+ * flattened positions [d_off[j], d_off[j+1]); its own (local, 0-based) sa or
+ * rank array sits at the same offsets of d_sa / d_rank, and its lcp array
+ * (n_j + 1 entries, lcp[0] = lcp[n_j] = 0) at d_lcp + d_off[j] + j.  Empty
+ * strings are allowed.  The outputs cover the flattened positions; lr_start
+ * and starts hold flattened positions (subtract d_off[j] for string-local
+ * ones).  The per-string results are exactly those of lr_query_all run on
+ * each string alone.  LLR's never run past their string (an lcp value is at
+ * most the suffix length), so compact LLR's of consecutive strings keep
+ * strictly increasing starts and ends and the flattened cover step needs
+ * no string boundaries; only Lemma 1 reads the string table.
+ */
+typedef struct {
+    int64_t num;                /* number of strings (>= 1) */
+    int64_t total;              /* d_off[num]: flattened positions, 1 <= total <= 2^31 - 2 */
+    const int64_t* d_off;       /* num + 1 device offsets, d_off[0] = 0, non-decreasing */
+    const int32_t* d_sa;        /* flattened local suffix arrays, or NULL */
+    const int32_t* d_rank;      /* flattened local rank arrays, or NULL (sa wins when both are given) */
+    const int32_t* d_lcp;       /* flattened local lcp arrays, total + num entries */
+} lr_batch_desc;
+
+lr_status lr_batch_query_all(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batch,
+                             int32_t* d_lr_len, int32_t* d_lr_start,
+                             int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
+                             int64_t* h_total);
+
+/*
+ * Autotuning.  Kernel shape choices (the cover tile: 2048 or 4096
+ * positions; the front end, when both sa and rank are given) are timed on
+ * the given batch (a single string is a batch with num = 1) and the fastest
+ * is remembered in the context for batches of the same shape class (total
+ * size and mean string length, both rounded to powers of two).  Later
+ * queries of that class use it.  *choice receives the chosen shape code
+ * (bit 0: 4096-position cover tile; bit 1: rank-gather front end).  The
+ * outputs are overwritten.  lr_autotune_save / _load write and read the
+ * remembered choices as a small text file (one "class code" pair per line).
+ */
+lr_status lr_autotune(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batch,
+                      int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
+                      int64_t starts_capacity, int32_t* choice);
+lr_status lr_autotune_save(lr_ctx* ctx, const char* path);
+lr_status lr_autotune_load(lr_ctx* ctx, const char* path);
+
+/*
+ * Captured plans: the launch sequence of one batched query with fixed
+ * inputs, outputs and sizes, captured once into a CUDA graph (with its own
+ * scratch, owned by the plan) and replayed by lr_plan_launch.  For batch
+ * shapes that repeat, it removes the per-launch host overhead.  The plan
+ * keeps the device pointers it was created with: refill those buffers in
+ * place between launches.  The shape is the context's tuned choice at
+ * creation time.  Launches of one plan must not overlap (they share its
+ * scratch): issue them on one stream.  lr_plan_launch only enqueues;
+ * lr_plan_result waits for the stream, stores the number of LR starts of
+ * the last launch in *h_total (when non-NULL) and reports its input errors
+ * (LR_ERR_SENTINEL), timeouts and LR_ERR_CAPACITY.  lr_plan_destroy waits
+ * for the device and frees everything the plan owns.
+ */
+typedef struct lr_plan lr_plan;
+lr_status lr_plan_create(lr_ctx* ctx, const lr_batch_desc* batch,
+                         int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
+                         int64_t starts_capacity, lr_plan** plan);
+lr_status lr_plan_launch(lr_plan* plan, lr_stream_t stream);
+lr_status lr_plan_result(lr_plan* plan, lr_stream_t stream, int64_t* h_total);
+lr_status lr_plan_destroy(lr_plan* plan);
+
+/*
  * lr_query_all_static -- lr_query_all for callers that cannot allocate.
  *
  * The paper has no counterpart of this entry point; it exists for library

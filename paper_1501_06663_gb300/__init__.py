@@ -31,10 +31,18 @@ EXPORTED = (
     "lr_create", "lr_destroy", "lr_status_str", "lr_last_cuda_error", "lr_device_status",
     "lr_query_leftmost", "lr_query_all", "lr_query_all_host", "lr_last_launch_count",
     "lr_set_phase_timing", "lr_phase_times", "lr_last_compact_size", "lr_query_all_static",
+    "lr_batch_query_all", "lr_autotune", "lr_autotune_save", "lr_autotune_load",
+    "lr_plan_create", "lr_plan_launch", "lr_plan_result", "lr_plan_destroy",
 )
 
 #: largest n lr_query_all_static takes (LR_STATIC_MAX_N in include/lr.h)
 LR_STATIC_MAX_N = 1 << 20
+
+
+class BatchDesc(ctypes.Structure):
+    """lr_batch_desc: a flattened table of strings (see include/lr.h)."""
+    _fields_ = [("num", ctypes.c_int64), ("total", ctypes.c_int64), ("d_off", ctypes.c_void_p),
+                ("d_sa", ctypes.c_void_p), ("d_rank", ctypes.c_void_p), ("d_lcp", ctypes.c_void_p)]
 
 
 class LRError(RuntimeError):
@@ -69,6 +77,15 @@ def load(path: str | None = None):
     lib.lr_phase_times.restype = i32
     lib.lr_last_compact_size.argtypes = [vp, vp, ctypes.POINTER(i64)]
     lib.lr_query_all_static.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    bd = ctypes.POINTER(BatchDesc)
+    lib.lr_batch_query_all.argtypes = [vp, vp, bd, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_autotune.argtypes = [vp, vp, bd, vp, vp, vp, vp, i64, ctypes.POINTER(i32)]
+    lib.lr_autotune_save.argtypes = [vp, ctypes.c_char_p]
+    lib.lr_autotune_load.argtypes = [vp, ctypes.c_char_p]
+    lib.lr_plan_create.argtypes = [vp, bd, vp, vp, vp, vp, i64, ctypes.POINTER(vp)]
+    lib.lr_plan_launch.argtypes = [vp, vp]
+    lib.lr_plan_result.argtypes = [vp, vp, ctypes.POINTER(i64)]
+    lib.lr_plan_destroy.argtypes = [vp]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -197,6 +214,64 @@ def lr_query_all_static(rank, lcp, lr_len, lr_start, offsets, starts, stream=Non
     return st, (tot.value if sync else None)
 
 
+def batch_desc(off, lcp, sa=None, rank=None) -> BatchDesc:
+    """lr_batch_desc over device tensors: off (int64, num + 1), lcp (int32,
+    total + num), sa / rank (int32, total; at least one)."""
+    num = int(off.numel()) - 1
+    total = int((sa if sa is not None else rank).numel())
+    return BatchDesc(num, total, _ptr(off), _ptr(sa), _ptr(rank), _ptr(lcp))
+
+
+def lr_batch_query_all(ctx, desc, lr_len, lr_start, offsets, starts, stream=None, sync=True):
+    """Batched all-LR query (flattened outputs).  Returns (status, total or None)."""
+    cap = int(starts.numel()) if starts is not None else 0
+    tot = ctypes.c_int64(-1)
+    st = load().lr_batch_query_all(ctx, _stream(stream), ctypes.byref(desc), _ptr(lr_len), _ptr(lr_start),
+                                   _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot) if sync else None)
+    return st, (tot.value if sync else None)
+
+
+def lr_autotune(ctx, desc, lr_len, lr_start, offsets, starts, stream=None) -> int:
+    """Times the shape choices on this batch; remembers and returns the fastest shape code."""
+    cap = int(starts.numel()) if starts is not None else 0
+    choice = ctypes.c_int32(-1)
+    _check(load().lr_autotune(ctx, _stream(stream), ctypes.byref(desc), _ptr(lr_len), _ptr(lr_start),
+                              _ptr(offsets), _ptr(starts), cap, ctypes.byref(choice)), "lr_autotune")
+    return choice.value
+
+
+def lr_autotune_save(ctx, path: str) -> None:
+    _check(load().lr_autotune_save(ctx, os.fsencode(path)), "lr_autotune_save")
+
+
+def lr_autotune_load(ctx, path: str) -> None:
+    _check(load().lr_autotune_load(ctx, os.fsencode(path)), "lr_autotune_load")
+
+
+def lr_plan_create(ctx, desc, lr_len, lr_start, offsets, starts):
+    """Captures one batched query into a replayable plan (a CUDA graph with its own scratch)."""
+    cap = int(starts.numel()) if starts is not None else 0
+    h = ctypes.c_void_p()
+    _check(load().lr_plan_create(ctx, ctypes.byref(desc), _ptr(lr_len), _ptr(lr_start), _ptr(offsets),
+                                 _ptr(starts), cap, ctypes.byref(h)), "lr_plan_create")
+    return h
+
+
+def lr_plan_launch(plan, stream=None) -> None:
+    _check(load().lr_plan_launch(plan, _stream(stream)), "lr_plan_launch")
+
+
+def lr_plan_result(plan, stream=None):
+    """Waits for the stream; returns (status, total LR starts of the last launch)."""
+    tot = ctypes.c_int64(-1)
+    st = load().lr_plan_result(plan, _stream(stream), ctypes.byref(tot))
+    return st, tot.value
+
+
+def lr_plan_destroy(plan) -> None:
+    _check(load().lr_plan_destroy(plan), "lr_plan_destroy")
+
+
 # ---------------------------------------------------------------- convenience
 
 class Context:
@@ -245,4 +320,26 @@ class Context:
             starts = torch.empty(total, dtype=torch.int32, device=dev)
             st, total = lr_query_all(self.handle, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream)
         _check(st, "lr_query_all")
+        return lr_len, lr_start, offsets, starts[:total]
+
+    def query_batch(self, off, lcp, sa=None, rank=None, capacity: int | None = None, stream=None):
+        """Batched all-LR query over a flattened string table (device tensors).
+
+        Returns flattened (lr_len, lr_start, offsets, starts[:total]); lr_start
+        and starts are flattened positions.
+        """
+        import torch
+        desc = batch_desc(off, lcp, sa=sa, rank=rank)
+        n = desc.total
+        dev = lcp.device
+        lr_len = torch.empty(n, dtype=torch.int32, device=dev)
+        lr_start = torch.empty(n, dtype=torch.int32, device=dev)
+        offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        cap = 2 * n + 1024 if capacity is None else int(capacity)
+        starts = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        st, total = lr_batch_query_all(self.handle, desc, lr_len, lr_start, offsets, starts, stream)
+        if st == LR_ERR_CAPACITY:
+            starts = torch.empty(total, dtype=torch.int32, device=dev)
+            st, total = lr_batch_query_all(self.handle, desc, lr_len, lr_start, offsets, starts, stream)
+        _check(st, "lr_batch_query_all")
         return lr_len, lr_start, offsets, starts[:total]

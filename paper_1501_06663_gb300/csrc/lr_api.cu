@@ -3,7 +3,9 @@
 // the query runs in the kernels of lr_query.cu.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
+#include <map>
 #include <new>
 #include "lr.h"
 #include "lr_internal.h"
@@ -24,6 +26,18 @@ struct lr_ctx {
     long long last_n = 0;                 // size of the last query (its tile_cbase[ntiles] is m)
     lr::PhaseEvents events;               // per-kernel timing (off by default)
     bool events_created = false;
+    std::map<int, int> tuned;             // shape class -> shape code (lr_autotune)
+};
+
+struct lr_plan {
+    int device = 0;
+    unsigned char* scratch = nullptr;     // the plan's own scratch
+    unsigned* d_err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int64_t* d_total = nullptr;     // d_offsets + total
+    int64_t capacity = 0;
+    long long* h_pinned = nullptr;        // 2 words: total, error bits
 };
 
 namespace {
@@ -53,7 +67,7 @@ lr_status cuda_fail(lr_ctx* ctx, cudaError_t e) {
 
 struct Layout {
     size_t off_status_g, off_status_b, off_status_o, off_cursor1, off_cursor2, zero_end;
-    size_t off_tile_cbase, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo, total;
+    size_t off_tile_cbase, off_tile_seg, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo, total;
 };
 
 Layout layout_for(long long n) {
@@ -66,7 +80,8 @@ Layout layout_for(long long n) {
     L.off_cursor2 = align_up(L.off_cursor1 + (size_t)ns * 4 * lr::kCursorStride);
     L.zero_end = L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride;
     L.off_tile_cbase = align_up(L.zero_end);
-    L.off_cstart = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
+    L.off_tile_seg = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
+    L.off_cstart = align_up(L.off_tile_seg + (size_t)nt * 4);
     L.off_cend = align_up(L.off_cstart + (size_t)n * 4);
     L.off_ent1 = align_up(L.off_cend + (size_t)n * 4);
     L.off_ent2 = align_up(L.off_ent1 + (size_t)ns * lr::kSuper * 4);
@@ -76,7 +91,34 @@ Layout layout_for(long long n) {
     return L;
 }
 
-// Grows the scratch to hold a query of n positions and fills `s`.
+// Points `s` at the regions of a scratch block laid out for cap_n positions,
+// for a query of n <= cap_n positions.
+void carve(unsigned char* b, long long cap_n, long long n, unsigned* d_err, lr::Scratch* s) {
+    const Layout L = layout_for(cap_n);
+    s->tickets = (unsigned*)b;
+    s->qerr = (unsigned*)(b + 16);
+    s->err = d_err;
+    s->status_g = (unsigned long long*)(b + L.off_status_g);
+    s->status_b = (unsigned long long*)(b + L.off_status_b);
+    s->status_o = (unsigned long long*)(b + L.off_status_o);
+    s->cursor1 = (unsigned*)(b + L.off_cursor1);
+    s->cursor2 = (unsigned*)(b + L.off_cursor2);
+    s->tile_cbase = (int32_t*)(b + L.off_tile_cbase);
+    s->tile_seg = (int32_t*)(b + L.off_tile_seg);
+    s->cstart = (int32_t*)(b + L.off_cstart);
+    s->cend = (int32_t*)(b + L.off_cend);
+    s->ent1 = (uint32_t*)(b + L.off_ent1);
+    s->ent2 = (uint32_t*)(b + L.off_ent2);
+    s->lbig = (int32_t*)(b + L.off_lbig);
+    s->halo = (int32_t*)(b + L.off_halo);
+    s->ntiles = lr::num_tiles(n);
+    s->nbuckets = lr::num_buckets(n);
+    s->nsupers = lr::num_supers(n);
+    s->zero_base = b;
+    s->zero_bytes = L.zero_end;          // covers the status words and cursors of any n <= cap_n
+}
+
+// Grows the context's scratch to hold a query of n positions and fills `s`.
 lr_status get_scratch(lr_ctx* ctx, long long n, lr::Scratch* s) {
     if (n > ctx->scratch_n) {
         const Layout L = layout_for(n);
@@ -93,32 +135,29 @@ lr_status get_scratch(lr_ctx* ctx, long long n, lr::Scratch* s) {
         ctx->scratch_bytes = L.total;
         ctx->scratch_n = n;
     }
-    // the regions are laid out for scratch_n; a smaller query uses their prefixes
-    const Layout L = layout_for(ctx->scratch_n);
-    unsigned char* b = ctx->scratch;
-    const long long nt = lr::num_tiles(n), nb = lr::num_buckets(n), ns = lr::num_supers(n);
-    s->tickets = (unsigned*)b;
-    s->qerr = (unsigned*)(b + 16);
-    s->err = ctx->d_err;
-    s->status_g = (unsigned long long*)(b + L.off_status_g);
-    s->status_b = (unsigned long long*)(b + L.off_status_b);
-    s->status_o = (unsigned long long*)(b + L.off_status_o);
-    s->cursor1 = (unsigned*)(b + L.off_cursor1);
-    s->cursor2 = (unsigned*)(b + L.off_cursor2);
-    s->tile_cbase = (int32_t*)(b + L.off_tile_cbase);
-    s->cstart = (int32_t*)(b + L.off_cstart);
-    s->cend = (int32_t*)(b + L.off_cend);
-    s->ent1 = (uint32_t*)(b + L.off_ent1);
-    s->ent2 = (uint32_t*)(b + L.off_ent2);
-    s->lbig = (int32_t*)(b + L.off_lbig);
-    s->halo = (int32_t*)(b + L.off_halo);
-    s->ntiles = nt;
-    s->nbuckets = nb;
-    s->nsupers = ns;
-    s->zero_base = b;
-    s->zero_bytes = L.zero_end;          // covers the status words and cursors of any n <= scratch_n
+    carve(ctx->scratch, ctx->scratch_n, n, ctx->d_err, s);
     ctx->last_n = n;
     return LR_OK;
+}
+
+// Shape class of a batch: log2 of the total and of the mean string length.
+int shape_class(long long total, long long num) {
+    auto lg = [](long long v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; };
+    const long long mean = num > 0 ? total / num : total;
+    return lg(total) * 64 + lg(mean > 0 ? mean : 1);
+}
+
+lr::Shape shape_of(int code) {
+    lr::Shape sh;
+    sh.cover_tiles_per = (code & 1) ? 2 : 1;
+    return sh;
+}
+
+// The tuned shape code for a batch (default: 4096-position cover tiles,
+// rank-order front end).
+int tuned_code(const lr_ctx* ctx, long long total, long long num) {
+    auto it = ctx->tuned.find(shape_class(total, num));
+    return it == ctx->tuned.end() ? 1 : it->second;
 }
 
 lr_status check_n(int32_t n) {
@@ -272,8 +311,10 @@ lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa
     lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
+    const lr::Shape shape = shape_of(tuned_code(ctx, n, 1));
     cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
-                                     (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
+                                     (cudaStream_t)stream, &ctx->last_launches, &ctx->events, lr::Segs{nullptr, 0},
+                                     shape);
     return e == cudaSuccess ? LR_OK : cuda_fail(ctx, e);
 }
 
@@ -288,8 +329,10 @@ lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa, con
     lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
+    const lr::Shape shape = shape_of(tuned_code(ctx, n, 1));
     cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
-                                     starts_capacity, true, (cudaStream_t)stream, &ctx->last_launches, &ctx->events);
+                                     starts_capacity, true, (cudaStream_t)stream, &ctx->last_launches, &ctx->events,
+                                     lr::Segs{nullptr, 0}, shape);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     if (!h_total) return LR_OK;
     st = sync_total(ctx, (cudaStream_t)stream, d_offsets + n, h_total);
@@ -353,6 +396,192 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_sa
         if (e != cudaSuccess) return cuda_fail(ctx, e);
     }
     return tot > starts_capacity ? LR_ERR_CAPACITY : LR_OK;
+}
+
+namespace {
+
+lr_status check_batch(const lr_batch_desc* b) {
+    if (!b || !b->d_off || !b->d_lcp || (!b->d_sa && !b->d_rank)) return LR_ERR_ARG;
+    if (b->num < 1 || b->total < 1 || b->total > kMaxN || b->num > b->total + 1) return LR_ERR_ARG;
+    return LR_OK;
+}
+
+lr_status batch_launch(lr_ctx* ctx, cudaStream_t stream, const lr_batch_desc* b, int code, int32_t* d_lr_len,
+                       int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts, int64_t cap) {
+    lr::Scratch s;
+    lr_status st = get_scratch(ctx, b->total, &s);
+    if (st != LR_OK) return st;
+    const bool use_rank = (code & 2) && b->d_rank;
+    const int32_t* sa = use_rank ? nullptr : b->d_sa;
+    const int32_t* rank = sa ? nullptr : b->d_rank;
+    cudaError_t e = lr::launch_query(sa, rank, b->d_lcp, (int32_t)b->total, s, d_lr_len, d_lr_start, d_offsets,
+                                     d_starts, cap, true, stream, &ctx->last_launches, &ctx->events,
+                                     lr::Segs{b->d_off, b->num}, shape_of(code));
+    return e == cudaSuccess ? LR_OK : cuda_fail(ctx, e);
+}
+
+}  // namespace
+
+lr_status lr_batch_query_all(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batch, int32_t* d_lr_len,
+                             int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
+                             int64_t* h_total) {
+    if (!ctx || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
+    if (starts_capacity < 0 || (starts_capacity > 0 && !d_starts)) return LR_ERR_ARG;
+    lr_status st = check_batch(batch);
+    if (st != LR_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    st = batch_launch(ctx, (cudaStream_t)stream, batch, tuned_code(ctx, batch->total, batch->num), d_lr_len,
+                      d_lr_start, d_offsets, d_starts, starts_capacity);
+    if (st != LR_OK || !h_total) return st;
+    st = sync_total(ctx, (cudaStream_t)stream, d_offsets + batch->total, h_total);
+    if (st != LR_OK) return st;
+    return (*h_total > starts_capacity) ? LR_ERR_CAPACITY : LR_OK;
+}
+
+lr_status lr_autotune(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batch, int32_t* d_lr_len,
+                      int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity,
+                      int32_t* choice) {
+    if (!ctx || !d_lr_len || !d_lr_start || !d_offsets || !choice) return LR_ERR_ARG;
+    lr_status st = check_batch(batch);
+    if (st != LR_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    cudaStream_t strm = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(ctx, cudaErrorUnknown);
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ctx, cudaErrorUnknown); }
+    int best = -1;
+    float best_ms = 0.f;
+    for (int code = 0; code < 4; ++code) {
+        const bool front_rank = code & 2;
+        if (front_rank && (!batch->d_rank || !batch->d_sa)) continue;   // only a choice when both are given
+        float acc = 0.f;
+        for (int rep = 0; rep < 4 && st == LR_OK; ++rep) {
+            cudaEventRecord(e0, strm);
+            st = batch_launch(ctx, strm, batch, code, d_lr_len, d_lr_start, d_offsets, d_starts, starts_capacity);
+            cudaEventRecord(e1, strm);
+            if (st != LR_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_fail(ctx, cudaErrorUnknown); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) acc += ms;                                        // first run warms up
+        }
+        if (st != LR_OK) break;
+        if (best < 0 || acc < best_ms) { best = code; best_ms = acc; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LR_OK) return st;
+    st = sync_total(ctx, strm, nullptr, nullptr);
+    if (st != LR_OK) return st;
+    ctx->tuned[shape_class(batch->total, batch->num)] = best;
+    *choice = best;
+    return LR_OK;
+}
+
+lr_status lr_autotune_save(lr_ctx* ctx, const char* path) {
+    if (!ctx || !path) return LR_ERR_ARG;
+    FILE* f = std::fopen(path, "w");
+    if (!f) return LR_ERR_ARG;
+    for (const auto& kv : ctx->tuned) std::fprintf(f, "%d %d\n", kv.first, kv.second);
+    std::fclose(f);
+    return LR_OK;
+}
+
+lr_status lr_autotune_load(lr_ctx* ctx, const char* path) {
+    if (!ctx || !path) return LR_ERR_ARG;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return LR_ERR_ARG;
+    int cls = 0, code = 0;
+    while (std::fscanf(f, "%d %d", &cls, &code) == 2)
+        if (code >= 0 && code < 4) ctx->tuned[cls] = code;
+    std::fclose(f);
+    return LR_OK;
+}
+
+lr_status lr_plan_create(lr_ctx* ctx, const lr_batch_desc* batch, int32_t* d_lr_len, int32_t* d_lr_start,
+                         int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity, lr_plan** out) {
+    if (!ctx || !out || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
+    if (starts_capacity < 0 || (starts_capacity > 0 && !d_starts)) return LR_ERR_ARG;
+    *out = nullptr;
+    lr_status st = check_batch(batch);
+    if (st != LR_OK) return st;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr_plan* plan = new (std::nothrow) lr_plan();
+    if (!plan) return LR_ERR_NOMEM;
+    plan->device = ctx->device;
+    plan->d_total = d_offsets + batch->total;
+    plan->capacity = starts_capacity;
+    const Layout L = layout_for(batch->total);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaMalloc((void**)&plan->scratch, L.total);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&plan->d_err, 256);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_err, 0, 256);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&plan->h_pinned, 2 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        lr::Scratch s;
+        carve(plan->scratch, batch->total, batch->total, plan->d_err, &s);
+        const int code = tuned_code(ctx, batch->total, batch->num);
+        const bool use_rank = (code & 2) && batch->d_rank;
+        const int32_t* sa = use_rank ? nullptr : batch->d_sa;
+        const int32_t* rank = sa ? nullptr : batch->d_rank;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = lr::launch_query(sa, rank, batch->d_lcp, (int32_t)batch->total, s, d_lr_len, d_lr_start,
+                                              d_offsets, d_starts, starts_capacity, true, cs, nullptr, nullptr,
+                                              lr::Segs{batch->d_off, batch->num}, shape_of(code));
+            e = cudaStreamEndCapture(cs, &plan->graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lr_plan_destroy(plan);
+        return cuda_fail(ctx, e);
+    }
+    *out = plan;
+    return LR_OK;
+}
+
+lr_status lr_plan_launch(lr_plan* plan, lr_stream_t stream) {
+    if (!plan || !plan->exec) return LR_ERR_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return LR_ERR_CUDA;
+    return cudaGraphLaunch(plan->exec, (cudaStream_t)stream) == cudaSuccess ? LR_OK : LR_ERR_CUDA;
+}
+
+lr_status lr_plan_result(lr_plan* plan, lr_stream_t stream, int64_t* h_total) {
+    if (!plan || !plan->exec) return LR_ERR_ARG;
+    DeviceGuard g(plan->device);
+    if (!g.ok) return LR_ERR_CUDA;
+    cudaStream_t strm = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&plan->h_pinned[0], plan->d_total, 8, cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&plan->h_pinned[1], plan->d_err, 4, cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->d_err, 0, 4, strm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+    if (e != cudaSuccess) { cudaGetLastError(); return LR_ERR_CUDA; }
+    if (h_total) *h_total = plan->h_pinned[0];
+    lr_status st = device_bits_to_status((unsigned)(plan->h_pinned[1] & 0xffffffffu));
+    if (st != LR_OK) return st;
+    return plan->h_pinned[0] > plan->capacity ? LR_ERR_CAPACITY : LR_OK;
+}
+
+lr_status lr_plan_destroy(lr_plan* plan) {
+    if (!plan) return LR_ERR_ARG;
+    DeviceGuard g(plan->device);
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->scratch) cudaFree(plan->scratch);
+    if (plan->d_err) cudaFree(plan->d_err);
+    if (plan->h_pinned) cudaFreeHost(plan->h_pinned);
+    delete plan;
+    return LR_OK;
 }
 
 }  // extern "C"

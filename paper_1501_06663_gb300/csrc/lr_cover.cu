@@ -4,8 +4,8 @@
 //
 // Starts and ends of LLRc strictly increase (Sec. 3.2), so the compact LLR's
 // covering a position k form a contiguous window of LLRc whose two ends only
-// move right as k grows.  Per tile of kCoverTile positions (tiles in order
-// by an atomic ticket):
+// move right as k grows.  Per tile of 2048 or 4096 positions (tiles in
+// order by an atomic ticket):
 //
 //  * the window range of the whole tile is LLRc[lo, cb1): the tile's own
 //    entries [cb0, cb1) plus the carry [lo, cb0), the earlier entries whose
@@ -33,11 +33,21 @@ namespace lr {
 
 namespace {
 
-constexpr int kWarps = kCoverThreads / kWarp;     // 16
-constexpr int kChunks = kCoverTile / kWarp;        // 128 runs of 32 positions
-constexpr int kChunksPerWarp = kChunks / kWarps;   // 8
+// Shape of a cover tile of kTile x TP positions run by kThreads x TP threads;
+// every warp owns 8 runs of 32 positions.
+template <int TP>
+struct Cfg {
+    static constexpr int kTileC = kTile * TP;
+    static constexpr int kThr = kThreads * TP;
+    static constexpr int kWarps = kThr / kWarp;
+    static constexpr int kChunks = kTileC / kWarp;
+    static constexpr int kChunksPerWarp = kChunks / kWarps;
+    static constexpr int kMinBlocks = TP == 1 ? 5 : 3;
+};
 
+template <int TP>
 struct __align__(16) CoverSmem {
+    static constexpr int kChunks = Cfg<TP>::kChunks;
     int32_t cs[kCoverCap];           // window range LLRc[lo, cb1): starts
     int32_t cl[kCoverCap];           //                             lengths
     unsigned smap[kChunks];          // bit x: an entry of the tile starts at k0 + x
@@ -52,6 +62,7 @@ struct __align__(16) CoverSmem {
 };
 
 // Exclusive prefix popcounts of the kChunks bitmap words, by one warp.
+template <int kChunks>
 __device__ __forceinline__ void popc_prefix(const unsigned* map, int32_t* pre) {
     constexpr int kPer = kChunks / kWarp;
     const int lane = lane_id();
@@ -64,6 +75,7 @@ __device__ __forceinline__ void popc_prefix(const unsigned* map, int32_t* pre) {
 }
 
 // Exclusive scan of the kChunks ints of a[] by one warp; returns the total.
+template <int kChunks>
 __device__ __forceinline__ int scan_chunks(int32_t* a) {
     constexpr int kPer = kChunks / kWarp;
     const int lane = lane_id();
@@ -79,15 +91,17 @@ __device__ __forceinline__ int scan_chunks(int32_t* a) {
 
 }  // namespace
 
-#ifndef LR_COVER_MIN_BLOCKS
-#define LR_COVER_MIN_BLOCKS 3
-#endif
-
-template <bool kAll>
-__global__ void __launch_bounds__(kCoverThreads, LR_COVER_MIN_BLOCKS)
+template <bool kAll, int TP>
+__global__ void __launch_bounds__(Cfg<TP>::kThr, Cfg<TP>::kMinBlocks)
 k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict__ lr_start,
         int64_t* __restrict__ offsets, int32_t* __restrict__ starts, long long capacity) {
-    __shared__ CoverSmem sm;
+    constexpr int kCoverTile = Cfg<TP>::kTileC;
+    constexpr int kCoverThreads = Cfg<TP>::kThr;
+    constexpr int kCoverTilesPer = TP;
+    constexpr int kWarps = Cfg<TP>::kWarps;
+    constexpr int kChunks = Cfg<TP>::kChunks;
+    constexpr int kChunksPerWarp = Cfg<TP>::kChunksPerWarp;
+    __shared__ CoverSmem<TP> sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) sm.tile = atomicAdd(&s.tickets[2], 1u);
     if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
@@ -167,8 +181,8 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         }
     }
     __syncthreads();
-    if (warp == 0) popc_prefix(sm.smap, sm.spre);
-    if (warp == 1) popc_prefix(sm.emap, sm.epre);
+    if (warp == 0) popc_prefix<kChunks>(sm.smap, sm.spre);
+    if (warp == 1) popc_prefix<kChunks>(sm.emap, sm.epre);
     __syncthreads();
 
     // candidate v of the range: start and length (shared memory, or LLRc in
@@ -240,7 +254,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         }
         __syncthreads();
         if (warp == 0) {
-            const int tot = scan_chunks(sm.chunk);
+            const int tot = scan_chunks<kChunks>(sm.chunk);
             if (lane == 0) {
                 publish(s.status_o, tile, tile == 0 ? kPrefix : kAggregate, tot);
                 sm.ttot = tot;
@@ -265,7 +279,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             if (lane == 0) {
                 if (tile != 0) publish(s.status_o, tile, kPrefix, ex + tot);
                 sm.obase = ex;
-                if (tile == num_cover_tiles(n) - 1) offsets[n] = ex + tot;
+                if (tile == num_cover_tiles(n, TP) - 1) offsets[n] = ex + tot;
             }
         }
         __syncthreads();
@@ -298,12 +312,20 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
 }
 
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
-                  int32_t* starts, long long capacity, bool all, cudaStream_t stream) {
-    const unsigned grid = (unsigned)num_cover_tiles(n);
-    if (all)
-        k_cover<true><<<grid, kCoverThreads, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
-    else
-        k_cover<false><<<grid, kCoverThreads, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
+                  int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream) {
+    if (tiles_per == 1) {
+        const unsigned grid = (unsigned)num_cover_tiles(n, 1);
+        if (all)
+            k_cover<true, 1><<<grid, Cfg<1>::kThr, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
+        else
+            k_cover<false, 1><<<grid, Cfg<1>::kThr, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
+    } else {
+        const unsigned grid = (unsigned)num_cover_tiles(n, 2);
+        if (all)
+            k_cover<true, 2><<<grid, Cfg<2>::kThr, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
+        else
+            k_cover<false, 2><<<grid, Cfg<2>::kThr, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
+    }
 }
 
 }  // namespace lr

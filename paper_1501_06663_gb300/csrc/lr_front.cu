@@ -48,14 +48,78 @@ __device__ __forceinline__ int warp_scan64(int32_t* a) {
     return __shfl_sync(kFull, incl, kWarp - 1);
 }
 
+// The strings of a batched query that overlap one CTA's flattened range
+// [g0, g1), with their offsets staged in shared memory when there are at
+// most kSegCap of them (else looked up in global memory).
+struct SegView {
+    const int64_t* off;      // global, num + 1 entries
+    long long* sh;           // shared, kSegCap + 1 entries
+    long long j0, j1;        // first and last string overlapping the range
+    bool staged;
+
+    // Called by the whole CTA (contains a barrier).
+    __device__ void stage(const Segs& segs, const Scratch& s, long long g0, long long g1, long long* smem) {
+        off = segs.off;
+        sh = smem;
+        // j1: the string holding the start of the tile after the range,
+        // which is at or after the string holding g1 - 1
+        const long long t0 = g0 / kTile, t1 = (g1 - 1) / kTile + 1;
+        j0 = s.tile_seg[t0];
+        j1 = (t1 < s.ntiles) ? s.tile_seg[t1] : segs.num - 1;
+        if (j1 < j0) j1 = j0;                          // only after a reported bad offset table
+        staged = (j1 - j0 + 2) <= kSegCap + 1;
+        if (staged)
+            for (long long i = threadIdx.x; i < j1 - j0 + 2; i += blockDim.x) sh[i] = __ldg(off + j0 + i);
+        __syncthreads();
+    }
+    __device__ __forceinline__ long long at(long long j) const { return staged ? sh[j - j0] : __ldg(off + j); }
+    // the string holding position g (j0 <= result <= j1); `hint` only moves forward
+    __device__ __forceinline__ long long find(long long g, long long hint) const {
+        if (staged) {
+            long long j = hint;
+            while (j < j1 && sh[j + 1 - j0] <= g) ++j;
+            return j;
+        }
+        long long lo = hint, hi = j1;                 // last j with off[j] <= g
+        while (lo < hi) {
+            const long long mid = (lo + hi + 1) >> 1;
+            if (__ldg(off + mid) <= g) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    }
+};
+
+// For every tile of kTile flattened positions, the string holding its first
+// position (the last j with off[j] <= tile start).
+__global__ void k_seg_index(int32_t n, Scratch s, Segs segs) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s.ntiles) return;
+    const long long g = t * kTile;
+    long long lo = 0, hi = segs.num - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (__ldg(segs.off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    s.tile_seg[t] = (int32_t)lo;
+    if (t == 0 && (__ldg(segs.off) != 0 || __ldg(segs.off + segs.num) != n)) report(s, kErrInput);
+    // offsets must not decrease
+    for (long long j = t; j < segs.num; j += s.ntiles)
+        if (__ldg(segs.off + j) > __ldg(segs.off + j + 1)) report(s, kErrInput);
+}
+
 }  // namespace
+
+void launch_seg_index(int32_t n, const Scratch& s, const Segs& segs, cudaStream_t stream) {
+    k_seg_index<<<(unsigned)((s.ntiles + 255) / 256), 256, 0, stream>>>(n, s, segs);
+}
 
 // ---------------------------------------------------------------------------
 // rank gather front end
 // ---------------------------------------------------------------------------
 
+template <bool kBatch>
 __global__ void __launch_bounds__(kThreads)
-k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, int32_t n, Scratch s) {
+k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs) {
     constexpr int kChunks = kTile / kWarp;          // 64 runs of 32 positions
     constexpr int kWarps = kThreads / kWarp;        // 8
     __shared__ int32_t Ls[kTile + 1];               // Ls[0] = L_{k0-1}, Ls[1+x] = L_{k0+x}
@@ -73,24 +137,42 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
 
     // Lemma 1.  rank is streamed; the lcp pair goes through L1 (one sector
     // for 7 of 8 rank values).  Invalid input is reported and clamped so
-    // every access stays in bounds.
+    // every access stays in bounds.  In a batch, position k of string j has
+    // its local rank at rank[k] and the string's lcp at lcp[off[j] + j ..].
     unsigned bad = 0;
+    __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
+    SegView sv{};
+    if constexpr (kBatch) {
+        const long long g1 = (k0 + kTile < n) ? k0 + kTile : n;
+        sv.stage(segs, s, k0 > 0 ? k0 - 1 : 0, g1, seg_sh);
+    }
+    long long hint = kBatch ? sv.j0 : 0;
     auto llr = [&](long long k) -> int32_t {
         uint32_t r = (uint32_t)__ldcs(rank + k);
-        if (r >= (uint32_t)n) { bad = 1; r = 0; }
-        const int32_t a = __ldg(lcp + r), b = __ldg(lcp + r + 1);
+        long long base = 0, nj = n, lbase = 0;
+        if constexpr (kBatch) {
+            hint = sv.find(k, hint);
+            base = sv.at(hint);
+            nj = sv.at(hint + 1) - base;
+            lbase = base + hint;
+            if (base < 0 || nj < 1 || base + nj > n || k < base) { bad = 1; return 0; }   // bad offset table
+        }
+        if (r >= (uint32_t)nj) { bad = 1; r = 0; }
+        const int32_t a = __ldg(lcp + lbase + r), b = __ldg(lcp + lbase + r + 1);
+        if (kBatch && ((r == 0 && a != 0) || ((long long)r == nj - 1 && b != 0))) bad = 1;   // lcp sentinels
         int32_t L = a > b ? a : b;
-        if (L < 0 || (long long)L > (long long)n - k) { bad = 1; L = 0; }
+        if (L < 0 || (long long)L > nj - (k - base)) { bad = 1; L = 0; }
         return L;
     };
+    if (tid == 0) {
+        Ls[0] = (k0 > 0) ? llr(k0 - 1) : 0;
+        if (!kBatch && tile == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
+    }
+    hint = kBatch ? sv.j0 : 0;
 #pragma unroll
     for (int j = 0; j < kTile / kThreads; ++j) {
         const int x = j * kThreads + tid;
         Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
-    }
-    if (tid == 0) {
-        Ls[0] = (k0 > 0) ? llr(k0 - 1) : 0;
-        if (tile == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
     }
     if (bad) report(s, kErrInput);
     __syncthreads();
@@ -139,8 +221,12 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
     }
 }
 
-void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream) {
-    k_gather_llr<<<(unsigned)s.ntiles, kThreads, 0, stream>>>(rank, lcp, n, s);
+void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
+                         cudaStream_t stream) {
+    if (segs.num > 0)
+        k_gather_llr<true><<<(unsigned)s.ntiles, kThreads, 0, stream>>>(rank, lcp, n, s, segs);
+    else
+        k_gather_llr<false><<<(unsigned)s.ntiles, kThreads, 0, stream>>>(rank, lcp, n, s, segs);
 }
 
 // ---------------------------------------------------------------------------
@@ -207,25 +293,48 @@ __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned
 // bucket order.  A length of 4095 or more is stored in lbig (field 4095);
 // the length of the last position of every bucket goes to halo (the next
 // bucket's predecessor).
+template <bool kBatch>
 __global__ void __launch_bounds__(kPartThreads, 2)
-k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s) {
+k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nb = (int)s.nsupers;                    // <= 2048
     const PartSmem P = part_smem(smem_raw, nb);
     for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
-    __syncthreads();
     const long long r0 = (long long)blockIdx.x * kPartRound;
+    __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
+    SegView sv{};
+    if constexpr (kBatch) sv.stage(segs, s, r0, (r0 + kPartRound < n) ? r0 + kPartRound : n, seg_sh);
+    __syncthreads();
     unsigned bad = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
+    if (!kBatch && blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
+    // In a batch, flattened rank index r of string j is local rank
+    // r - off[j]; its suffix starts at off[j] + sa[r] and its lcp pair is at
+    // lcp[off[j] + j + (r - off[j]) ..].  Positions are flattened.
     uint32_t p[kPartPer];
     int32_t L[kPartPer];
+    long long hint = kBatch ? sv.j0 : 0;
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const long long r = r0 + (long long)j * kPartThreads + threadIdx.x;
         if (r < n) {
-            p[j] = (uint32_t)__ldcs(sa + r);
-            const int32_t a = __ldcs(lcp + r), c = __ldg(lcp + r + 1);
-            L[j] = a > c ? a : c;
+            uint32_t pl = (uint32_t)__ldcs(sa + r);
+            long long base = 0, nj = n, lidx = r;
+            if constexpr (kBatch) {
+                hint = sv.find(r, hint);
+                base = sv.at(hint);
+                nj = sv.at(hint + 1) - base;
+                lidx = r + hint;
+                if (base < 0 || nj < 1 || base + nj > n || r < base) {     // bad offset table
+                    bad = 1; p[j] = 0xffffffffu; L[j] = 0; continue;
+                }
+            }
+            const int32_t a = __ldcs(lcp + lidx), c = __ldg(lcp + lidx + 1);
+            if (kBatch && ((r == base && a != 0) || (r == base + nj - 1 && c != 0))) bad = 1;   // lcp sentinels
+            int32_t Lj = a > c ? a : c;
+            if (pl >= (uint32_t)nj) { bad = 1; pl = 0xffffffffu; }
+            else if (Lj < 0 || (long long)Lj > nj - pl) { bad = 1; Lj = 0; }
+            p[j] = (pl == 0xffffffffu) ? pl : (uint32_t)(base + pl);
+            L[j] = Lj;
         } else {
             p[j] = 0xffffffffu; L[j] = 0;
         }
@@ -238,8 +347,7 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
         if (r >= n) continue;
         const uint32_t pj = p[j];
         if (pj >= (uint32_t)n) { bad = 1; continue; }
-        int32_t Lj = L[j];
-        if (Lj < 0 || (long long)Lj > (long long)n - pj) { bad = 1; Lj = 0; }
+        const int32_t Lj = L[j];
         uint32_t field = (uint32_t)Lj;
         if (field >= kEsc12) { field = kEsc12; s.lbig[pj] = Lj; }
         if ((pj & (kBucket - 1)) == kBucket - 1) s.halo[(pj >> kBucketLog) + 1] = Lj;
@@ -446,9 +554,13 @@ k_bucket_llr(int32_t n, Scratch s) {
 
 size_t bucket_smem_bytes() { return (size_t)kBucket * 2 + (size_t)(kBucket / kWarp) * 8; }
 
-void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream) {
+void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
+                      cudaStream_t stream) {
     const unsigned g1 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
-    k_part1<<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s);
+    if (segs.num > 0)
+        k_part1<true><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs);
+    else
+        k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs);
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
     k_part2<<<g2, kPartThreads, part_smem_bytes(kSubPerSuper), stream>>>(n, s);
 }
@@ -461,7 +573,9 @@ cudaError_t configure_front() {
     cudaError_t e = cudaFuncSetAttribute(k_bucket_llr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bucket_smem_bytes());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_part1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
+    e = cudaFuncSetAttribute(k_part1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_part1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_part2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)part_smem_bytes(kSubPerSuper));

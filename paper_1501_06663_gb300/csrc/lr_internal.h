@@ -9,13 +9,7 @@ namespace lr {
 // Tiles of the gather front end (and the granularity of tile_cbase).
 constexpr int kTile = 2048;          // positions per tile (one CTA)
 constexpr int kThreads = 256;        // threads per tile CTA
-// Tiles of the cover kernel: kCoverTilesPer front-end tiles each.
-#ifndef LR_COVER_TILES_PER
-#define LR_COVER_TILES_PER 2
-#endif
-constexpr int kCoverTilesPer = LR_COVER_TILES_PER;
-constexpr int kCoverTile = kTile * kCoverTilesPer;   // 4096 positions
-constexpr int kCoverThreads = kThreads * kCoverTilesPer;
+// Tiles of the cover kernel: kTile x (1 or 2) positions, kThreads x the same threads.
 constexpr int kCoverCap = 4096;      // compact LLR's a cover tile stages in shared memory
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
@@ -50,6 +44,7 @@ struct Scratch {
     unsigned* cursor2;             // fill counts of ent2, one per kCursorStride words (cleared per query)
     int32_t* lbig;                 // n: L of positions whose length field escaped
     int32_t* halo;                 // nbuckets + 1: L of the position before each bucket
+    int32_t* tile_seg;             // ntiles: first string overlapping each tile (batched queries)
     long long ntiles;
     long long nbuckets;
     long long nsupers;
@@ -58,7 +53,9 @@ struct Scratch {
 };
 
 __host__ __device__ inline long long num_tiles(long long n) { return (n + kTile - 1) / kTile; }
-__host__ __device__ inline long long num_cover_tiles(long long n) { return (n + kCoverTile - 1) / kCoverTile; }
+__host__ __device__ inline long long num_cover_tiles(long long n, int tiles_per) {
+    return (n + (long long)kTile * tiles_per - 1) / ((long long)kTile * tiles_per);
+}
 inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
 inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
 
@@ -72,19 +69,37 @@ struct PhaseEvents {
     int count = 0;                 // phases recorded by the last query
 };
 
+// Strings of a batched query: string j occupies the flattened positions
+// [off[j], off[j+1]); its local sa / rank live at the same offsets, its lcp
+// (n_j + 1 entries) at off[j] + j.  num == 0 means one string, no table.
+struct Segs {
+    const int64_t* off;            // device, num + 1 entries
+    long long num;
+};
+constexpr int kSegCap = 1024;      // strings per CTA a front end keeps in shared memory
+
+// Kernel shape choices a query can take (picked by lr_autotune_*).
+struct Shape {
+    int cover_tiles_per = 2;       // cover tile = kTile x this (1 or 2)
+};
+
 // Launches the whole query on `stream`: the front end (rank-order when sa is
 // non-null, else the rank gather) and the cover kernel.
 cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
                          int32_t* lr_len, int32_t* lr_start, int64_t* offsets, int32_t* starts,
                          long long capacity, bool all, cudaStream_t stream, int* launches,
-                         PhaseEvents* events);
+                         PhaseEvents* events, const Segs& segs = Segs{nullptr, 0}, const Shape& shape = Shape{});
 
 // Front ends (lr_front.cu) and the cover kernel (lr_cover.cu).
-void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream);
-void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, cudaStream_t stream);
+void launch_seg_index(int32_t n, const Scratch& s, const Segs& segs, cudaStream_t stream);
+void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
+                         cudaStream_t stream);
+void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
+                      cudaStream_t stream);
 void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream);
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
-                  int32_t* starts, long long capacity, bool all, cudaStream_t stream);
+                  int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream);
+
 cudaError_t configure_kernels();
 
 }  // namespace lr

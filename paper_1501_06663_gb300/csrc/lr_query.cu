@@ -14,25 +14,26 @@ cudaError_t configure_kernels() { return configure_front(); }
 cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
                          int32_t* lr_len, int32_t* lr_start, int64_t* offsets, int32_t* starts,
                          long long capacity, bool all, cudaStream_t stream, int* launches,
-                         PhaseEvents* events) {
+                         PhaseEvents* events, const Segs& segs, const Shape& shape) {
     cudaError_t e = cudaMemsetAsync(s.zero_base, 0, s.zero_bytes, stream);
     if (e != cudaSuccess) return e;
     const bool timed = events && events->enabled;
     int k = 0;
     auto mark = [&]() { if (timed) cudaEventRecord(events->ev[k], stream); ++k; };
+    if (segs.num > 0) launch_seg_index(n, s, segs, stream);                     // k_seg_index
     if (sa) {
         mark();
-        launch_partition(sa, lcp, n, s, stream);      // k_part1, k_part2
+        launch_partition(sa, lcp, n, s, segs, stream);      // k_part1, k_part2
         mark();
-        launch_bucket_front(n, s, stream);            // k_bucket_llr
+        launch_bucket_front(n, s, stream);                  // k_bucket_llr
     } else {
         mark();
-        launch_gather_front(rank, lcp, n, s, stream); // k_gather_llr
+        launch_gather_front(rank, lcp, n, s, segs, stream); // k_gather_llr
     }
     mark();
-    launch_cover(n, s, lr_len, lr_start, offsets, starts, capacity, all, stream);   // k_cover
+    launch_cover(n, s, lr_len, lr_start, offsets, starts, capacity, all, shape.cover_tiles_per, stream);
     if (timed) cudaEventRecord(events->ev[k], stream);
-    if (launches) *launches = sa ? 4 : 2;
+    if (launches) *launches = (sa ? 4 : 2) + (segs.num > 0 ? 1 : 0);
     if (events) events->count = k;
     return cudaGetLastError();
 }

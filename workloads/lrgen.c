@@ -437,6 +437,7 @@ void prep_lcp(const uint8_t* s, int64_t n, const int32_t* sa, const int32_t* ran
 
 /* Suffix, rank and lcp arrays of s; rank must hold n entries, lcp n+1. */
 int prep_all(const uint8_t* s, int64_t n, int32_t* sa, int32_t* rank, int32_t* lcp) {
+    if (n == 0) { lcp[0] = 0; return 0; }   /* empty string: its lcp array is the one sentinel */
     int rc = prep_sa(s, n, sa, rank);
     if (rc) return rc;
     prep_lcp(s, n, sa, rank, lcp);
