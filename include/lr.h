@@ -200,6 +200,95 @@ lr_status lr_plan_result(lr_plan* plan, lr_stream_t stream, int64_t* h_total);
 lr_status lr_plan_destroy(lr_plan* plan);
 
 /*
+ * Serving: a request loop with continuous batching (no paper counterpart;
+ * it drives the batched query of lr_batch_query_all).
+ *
+ * The server owns `slots` batch slots in device memory, each holding the
+ * inputs, outputs and scratch of one batch of up to max_batch_positions
+ * positions and max_batch_jobs jobs.  At start it sizes them from the free
+ * HBM (hbm_fraction of what cudaMemGetInfo reports) and fails with
+ * LR_ERR_NOMEM if not even one slot fits.  A submitted job waits in a queue
+ * until the slot being filled has room for it (HBM-based admission); its
+ * sa (or rank) and lcp are then copied to the device and stay resident in
+ * the slot until its results are back in host memory.  The slot being
+ * filled is closed and launched (one batched query, then a kernel that
+ * makes every job's results string-local) when it is full, when fewer than
+ * max_inflight slots are on the GPU, or when its oldest job has waited
+ * batch_window_us.  Jobs that arrive while other slots run are admitted into
+ * the next slot, and the copies of one slot overlap the kernels of another
+ * (one CUDA stream per slot).  A batch whose device checks report an input
+ * error is re-run one job at a time so that only the offending job fails.
+ * Each job's results equal those of lr_query_all on that job alone.
+ *
+ * A worker thread inside the library runs the loop; all functions here are
+ * thread-safe.  Host buffers of a job must stay valid until the job is done
+ * or cancelled; page-locked (pinned) buffers let the copies run
+ * asynchronously.
+ */
+typedef struct lr_server lr_server;
+
+typedef struct {
+    int32_t device;
+    int32_t slots;                 /* batch slots; 0 = 4 */
+    int32_t max_inflight;          /* slots on the GPU at once; 0 = 2 */
+    int64_t max_batch_positions;   /* positions per slot; 0 = 2^26 */
+    int32_t max_batch_jobs;        /* jobs per slot; 0 = 4096 */
+    int32_t max_queue;             /* queued jobs before lr_server_submit answers LR_ERR_BUSY; 0 = 65536 */
+    int32_t batch_window_us;       /* longest wait of an admitted job while other slots run; 0 = 2000 */
+    double hbm_fraction;           /* share of the free device memory the slots may take; 0 = 0.5 */
+    double starts_factor;          /* initial starts buffer of a slot, in entries per position; 0 = 2
+                                      (it grows, within the budget, when a batch needs more) */
+} lr_server_config;
+
+typedef struct {
+    const int32_t* h_sa;           /* host, n entries, or NULL */
+    const int32_t* h_rank;         /* host, n entries, or NULL (sa wins when both are given) */
+    const int32_t* h_lcp;          /* host, n + 1 entries */
+    int32_t n;                     /* 1 <= n <= max_batch_positions */
+    int32_t* h_lr_len;             /* host outputs, as lr_query_all: n */
+    int32_t* h_lr_start;           /* n, string-local positions */
+    int64_t* h_offsets;            /* n + 1 */
+    int32_t* h_starts;             /* starts_capacity entries (NULL when 0) */
+    int64_t starts_capacity;
+} lr_job;
+
+enum { LR_JOB_QUEUED = 0, LR_JOB_ADMITTED = 1, LR_JOB_RUNNING = 2, LR_JOB_DONE = 3, LR_JOB_CANCELLED = 4 };
+
+typedef struct {
+    int64_t submitted, completed, cancelled, failed;   /* jobs */
+    int64_t batches, positions;                        /* batches launched, positions completed */
+    double p50_us, p99_us, mean_us, max_us;            /* submit-to-done latency of completed jobs */
+    int32_t slots;
+    int64_t slot_positions;
+    int64_t device_bytes;                              /* device memory the server holds */
+} lr_server_stats;
+
+/* Starts the worker thread.  cfg may be NULL (all defaults, device 0). */
+lr_status lr_server_start(const lr_server_config* cfg, lr_server** server);
+/* Queues a job; *job_id identifies it.  LR_ERR_BUSY: the queue is full;
+ * LR_ERR_NOMEM: the job can never fit a slot; LR_ERR_ARG: bad job. */
+lr_status lr_server_submit(lr_server* server, const lr_job* job, int64_t* job_id);
+/* Non-blocking: *state = LR_JOB_*.  For a done job *result is its status
+ * (LR_OK; LR_ERR_CAPACITY with *total the needed size, lr_len, lr_start and
+ * offsets still written; LR_ERR_SENTINEL for bad input ...) and *total its
+ * number of LR starts.  A job's record is dropped once poll or wait has
+ * reported it done or cancelled (later calls on its id: LR_ERR_ARG).
+ * result and total may be NULL. */
+lr_status lr_server_poll(lr_server* server, int64_t job_id, int32_t* state, lr_status* result, int64_t* total);
+/* Waits up to timeout_ms (< 0: no limit) until the job is done or
+ * cancelled; LR_ERR_TIMEOUT if it is not.  Outputs as for poll (state may
+ * be NULL). */
+lr_status lr_server_wait(lr_server* server, int64_t job_id, int32_t timeout_ms, int32_t* state,
+                         lr_status* result, int64_t* total);
+/* Cancels a job still in the queue; LR_ERR_BUSY once it has been admitted. */
+lr_status lr_server_cancel(lr_server* server, int64_t job_id);
+/* Counters and latency percentiles; reset != 0 clears them afterwards. */
+lr_status lr_server_stats_get(lr_server* server, int32_t reset, lr_server_stats* stats);
+/* Cancels queued jobs, finishes admitted ones, stops the thread and frees
+ * everything the server holds. */
+lr_status lr_server_stop(lr_server* server);
+
+/*
  * lr_query_all_static -- lr_query_all for callers that cannot allocate.
  *
  * The paper has no counterpart of this entry point; it exists for library

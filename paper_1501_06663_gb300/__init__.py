@@ -33,7 +33,11 @@ EXPORTED = (
     "lr_set_phase_timing", "lr_phase_times", "lr_last_compact_size", "lr_query_all_static",
     "lr_batch_query_all", "lr_autotune", "lr_autotune_save", "lr_autotune_load",
     "lr_plan_create", "lr_plan_launch", "lr_plan_result", "lr_plan_destroy",
+    "lr_server_start", "lr_server_submit", "lr_server_poll", "lr_server_wait", "lr_server_cancel",
+    "lr_server_stats_get", "lr_server_stop",
 )
+
+LR_JOB_QUEUED, LR_JOB_ADMITTED, LR_JOB_RUNNING, LR_JOB_DONE, LR_JOB_CANCELLED = range(5)
 
 #: largest n lr_query_all_static takes (LR_STATIC_MAX_N in include/lr.h)
 LR_STATIC_MAX_N = 1 << 20
@@ -43,6 +47,29 @@ class BatchDesc(ctypes.Structure):
     """lr_batch_desc: a flattened table of strings (see include/lr.h)."""
     _fields_ = [("num", ctypes.c_int64), ("total", ctypes.c_int64), ("d_off", ctypes.c_void_p),
                 ("d_sa", ctypes.c_void_p), ("d_rank", ctypes.c_void_p), ("d_lcp", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    """lr_server_config (zeros mean defaults, see include/lr.h)."""
+    _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("max_batch_positions", ctypes.c_int64), ("max_batch_jobs", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("batch_window_us", ctypes.c_int32), ("hbm_fraction", ctypes.c_double),
+                ("starts_factor", ctypes.c_double)]
+
+
+class Job(ctypes.Structure):
+    """lr_job: one query job with host buffers."""
+    _fields_ = [("h_sa", ctypes.c_void_p), ("h_rank", ctypes.c_void_p), ("h_lcp", ctypes.c_void_p),
+                ("n", ctypes.c_int32), ("h_lr_len", ctypes.c_void_p), ("h_lr_start", ctypes.c_void_p),
+                ("h_offsets", ctypes.c_void_p), ("h_starts", ctypes.c_void_p), ("starts_capacity", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("batches", ctypes.c_int64), ("positions", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("slots", ctypes.c_int32), ("slot_positions", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
 
 
 class LRError(RuntimeError):
@@ -86,6 +113,13 @@ def load(path: str | None = None):
     lib.lr_plan_launch.argtypes = [vp, vp]
     lib.lr_plan_result.argtypes = [vp, vp, ctypes.POINTER(i64)]
     lib.lr_plan_destroy.argtypes = [vp]
+    lib.lr_server_start.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.lr_server_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(i64)]
+    lib.lr_server_poll.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(ci), ctypes.POINTER(i64)]
+    lib.lr_server_wait.argtypes = [vp, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(ci), ctypes.POINTER(i64)]
+    lib.lr_server_cancel.argtypes = [vp, i64]
+    lib.lr_server_stats_get.argtypes = [vp, i32, ctypes.POINTER(ServerStats)]
+    lib.lr_server_stop.argtypes = [vp]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -272,6 +306,49 @@ def lr_plan_destroy(plan) -> None:
     _check(load().lr_plan_destroy(plan), "lr_plan_destroy")
 
 
+def lr_server_start(cfg: ServerConfig | None = None):
+    h = ctypes.c_void_p()
+    _check(load().lr_server_start(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
+           "lr_server_start")
+    return h
+
+
+def lr_server_submit(server, job: Job):
+    """Returns (status, job id)."""
+    jid = ctypes.c_int64(-1)
+    st = load().lr_server_submit(server, ctypes.byref(job), ctypes.byref(jid))
+    return st, jid.value
+
+
+def lr_server_poll(server, job_id: int):
+    """Returns (status, state, result, total)."""
+    state, res, tot = ctypes.c_int32(-1), ctypes.c_int(-1), ctypes.c_int64(-1)
+    st = load().lr_server_poll(server, job_id, ctypes.byref(state), ctypes.byref(res), ctypes.byref(tot))
+    return st, state.value, res.value, tot.value
+
+
+def lr_server_wait(server, job_id: int, timeout_ms: int = -1):
+    """Returns (status, state, result, total)."""
+    state, res, tot = ctypes.c_int32(-1), ctypes.c_int(-1), ctypes.c_int64(-1)
+    st = load().lr_server_wait(server, job_id, timeout_ms, ctypes.byref(state), ctypes.byref(res),
+                               ctypes.byref(tot))
+    return st, state.value, res.value, tot.value
+
+
+def lr_server_cancel(server, job_id: int) -> int:
+    return load().lr_server_cancel(server, job_id)
+
+
+def lr_server_stats_get(server, reset: bool = False) -> dict:
+    s = ServerStats()
+    _check(load().lr_server_stats_get(server, 1 if reset else 0, ctypes.byref(s)), "lr_server_stats_get")
+    return {name: getattr(s, name) for name, _ in ServerStats._fields_}
+
+
+def lr_server_stop(server) -> None:
+    _check(load().lr_server_stop(server), "lr_server_stop")
+
+
 # ---------------------------------------------------------------- convenience
 
 class Context:
@@ -343,3 +420,71 @@ class Context:
             st, total = lr_batch_query_all(self.handle, desc, lr_len, lr_start, offsets, starts, stream)
         _check(st, "lr_batch_query_all")
         return lr_len, lr_start, offsets, starts[:total]
+
+
+class Server:
+    """A liblr serving loop (continuous batching) with host-buffer jobs.
+
+    submit() takes host arrays (numpy or CPU tensors; page-locked ones let
+    the copies run asynchronously) and allocates the job's host outputs
+    (starts: 4n + 1024 entries unless `capacity` is given; a job that needs
+    more finishes with LR_ERR_CAPACITY and its total); the arrays are kept
+    alive until the job's result is taken with wait().
+    """
+
+    def __init__(self, device: int = 0, **cfg):
+        c = ServerConfig(device=device)
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.handle = lr_server_start(c)
+        self._jobs = {}
+
+    def submit(self, lcp, sa=None, rank=None, capacity: int | None = None, pinned: bool = False):
+        """Queues one job; returns its id (raises LRError on LR_ERR_BUSY / NOMEM / ARG)."""
+        import numpy as np
+        n = int(len(sa) if sa is not None else len(rank))
+        cap = 4 * n + 1024 if capacity is None else int(capacity)
+        if pinned:
+            import torch
+            outs = (torch.empty(n, dtype=torch.int32, pin_memory=True),
+                    torch.empty(n, dtype=torch.int32, pin_memory=True),
+                    torch.empty(n + 1, dtype=torch.int64, pin_memory=True),
+                    torch.empty(max(cap, 1), dtype=torch.int32, pin_memory=True))
+        else:
+            outs = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n + 1, np.int64),
+                    np.empty(max(cap, 1), np.int32))
+        job = Job(_ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), _ptr(outs[3]),
+                  cap)
+        st, jid = lr_server_submit(self.handle, job)
+        _check(st, "lr_server_submit")
+        self._jobs[jid] = (sa, rank, lcp, outs)
+        return jid
+
+    def wait(self, job_id: int, timeout_ms: int = -1):
+        """(result status, lr_len, lr_start, offsets, starts[:total]) of a finished job (host arrays)."""
+        st, state, res, total = lr_server_wait(self.handle, job_id, timeout_ms)
+        _check(st, "lr_server_wait")
+        _, _, _, outs = self._jobs.pop(job_id)
+        if state == LR_JOB_CANCELLED:
+            return LR_ERR_BUSY, None, None, None, None
+        conv = [o.numpy() if hasattr(o, "numpy") else o for o in outs]
+        k = total if res == LR_OK else 0
+        return res, conv[0], conv[1], conv[2], conv[3][:k]
+
+    def cancel(self, job_id: int) -> int:
+        return lr_server_cancel(self.handle, job_id)
+
+    def stats(self, reset: bool = False) -> dict:
+        return lr_server_stats_get(self.handle, reset)
+
+    def close(self):
+        if self.handle is not None:
+            lr_server_stop(self.handle)
+            self.handle = None
+            self._jobs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -140,6 +140,20 @@ lr_status get_scratch(lr_ctx* ctx, long long n, lr::Scratch* s) {
     return LR_OK;
 }
 
+}  // namespace
+
+namespace lr {
+
+size_t scratch_size(long long n) { return layout_for(n).total; }
+
+void carve_scratch(unsigned char* base, long long cap_n, long long n, unsigned* d_err, Scratch* s) {
+    carve(base, cap_n, n, d_err, s);
+}
+
+}  // namespace lr
+
+namespace {
+
 // Shape class of a batch: log2 of the total and of the mean string length.
 int shape_class(long long total, long long num) {
     auto lg = [](long long v) { int k = 0; while (v > 1) { v >>= 1; ++k; } return k; };
@@ -172,6 +186,14 @@ lr_status device_bits_to_status(unsigned bits) {
 
 // Copies the total (offsets[n]) and the error bits to the host, waits, and
 // clears the error word.
+}  // namespace
+
+namespace lr {
+lr_status status_of_bits(unsigned bits) { return device_bits_to_status(bits); }
+}  // namespace lr
+
+namespace {
+
 lr_status sync_total(lr_ctx* ctx, cudaStream_t stream, const int64_t* d_total, int64_t* h_total) {
     cudaError_t e = cudaSuccess;
     if (d_total) e = cudaMemcpyAsync(&ctx->h_pinned[0], d_total, 8, cudaMemcpyDeviceToHost, stream);

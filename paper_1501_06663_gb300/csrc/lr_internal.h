@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include "lr.h"
 
 namespace lr {
 
@@ -101,5 +102,12 @@ void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_star
                   int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream);
 
 cudaError_t configure_kernels();
+
+// Scratch management (lr_api.cu): bytes of a scratch block for n positions,
+// and the carving of such a block (laid out for cap_n >= n) into `s`.
+size_t scratch_size(long long n);
+void carve_scratch(unsigned char* base, long long cap_n, long long n, unsigned* d_err, Scratch* s);
+// The lr_status for the device error bits of a query.
+lr_status status_of_bits(unsigned bits);
 
 }  // namespace lr

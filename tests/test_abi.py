@@ -60,3 +60,24 @@ def test_kernels_target_sm103a(lib_path):
     if out.returncode != 0:
         pytest.skip("cuobjdump unavailable")
     assert "sm_103a" in out.stdout
+
+
+def test_server_entry_points_without_gpu(lib_path):
+    """With no device the server refuses to start; NULL handles are argument errors."""
+    import ctypes
+    lib = lr.load()
+    h = ctypes.c_void_p()
+    cfg = lr.ServerConfig(device=0)
+    st = lib.lr_server_start(ctypes.byref(cfg), ctypes.byref(h))
+    if st == lr.LR_OK:                      # a GPU is present after all
+        assert lib.lr_server_stop(h) == lr.LR_OK
+    else:
+        assert st == lr.LR_ERR_CUDA
+    bad = lr.ServerConfig(device=0, hbm_fraction=2.0)
+    assert lib.lr_server_start(ctypes.byref(bad), ctypes.byref(h)) == lr.LR_ERR_ARG
+    null = ctypes.c_void_p(0)
+    jid = ctypes.c_int64()
+    assert lib.lr_server_submit(null, None, ctypes.byref(jid)) == lr.LR_ERR_ARG
+    assert lib.lr_server_cancel(null, 1) == lr.LR_ERR_ARG
+    assert lib.lr_server_stop(null) == lr.LR_ERR_ARG
+    assert lib.lr_plan_launch(null, null) == lr.LR_ERR_ARG
