@@ -181,6 +181,191 @@ def cpu_oracle_rate(w, target_s: float, seed: int = 0):
     return block / dt / 1e9, block, a, dt
 
 
+# --------------------------------------------------------------------------- batched and serving legs
+
+def _event_ms(stream, fn, reps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_leg(lr, dev, stream, count: int, reps: int):
+    """The batched mix (log-uniform lengths 1 Ki - 4 Mi, half DNA with planted
+    repeats, half protein with tandem repeats) in one batched query, tuned and
+    as a captured plan, against one lr_query_all launch per string."""
+    import torch
+
+    import workloads as W
+    text, off, _ = W.batched_mix(count=count, lo=1024, hi=4 * W.MI, seed=4)
+    sa, rank, lcp = W.prep_many(text, off)
+    del text
+    total = int(off[-1])
+    d_off, d_sa, d_rank, d_lcp = (torch.from_numpy(a).to(dev) for a in (off, sa, rank, lcp))
+    del sa, rank, lcp
+    ln = torch.empty(total, dtype=torch.int32, device=dev)
+    st = torch.empty(total, dtype=torch.int32, device=dev)
+    offs = torch.empty(total + 1, dtype=torch.int64, device=dev)
+    ctx = lr.lr_create(dev.index)
+    desc = lr.batch_desc(d_off, d_lcp, sa=d_sa)
+    s, tot = lr.lr_batch_query_all(ctx, desc, ln, st, offs, torch.empty(1, dtype=torch.int32, device=dev), stream)
+    if s not in (lr.LR_OK, lr.LR_ERR_CAPACITY):
+        raise lr.LRError(s, "lr_batch_query_all")
+    starts = torch.empty(max(tot, 1), dtype=torch.int32, device=dev)
+
+    def batched(d=desc):
+        r, _ = lr.lr_batch_query_all(ctx, d, ln, st, offs, starts, stream, sync=False)
+        if r != lr.LR_OK:
+            raise lr.LRError(r, "lr_batch_query_all")
+
+    batched_ms = _event_ms(stream, batched, reps)
+    both = lr.batch_desc(d_off, d_lcp, sa=d_sa, rank=d_rank)
+    code = lr.lr_autotune(ctx, both, ln, st, offs, starts, stream)
+    tuned_ms = _event_ms(stream, lambda: batched(both), reps)
+    plan = lr.lr_plan_create(ctx, both, ln, st, offs, starts)
+    plan_ms = _event_ms(stream, lambda: lr.lr_plan_launch(plan, stream), reps)
+    lr.lr_plan_destroy(plan)
+    if lr.lr_device_status(ctx, stream) != lr.LR_OK:
+        raise RuntimeError("batched leg: device error")
+
+    # one lr_query_all per string, on views of the same device arrays
+    h_off = off.tolist()
+    flat_off = offs.cpu().numpy()
+    offs2 = torch.empty(total + count, dtype=torch.int64, device=dev)
+    views = []
+    for j in range(count):
+        a, b = h_off[j], h_off[j + 1]
+        o0, o1 = int(flat_off[a]), int(flat_off[b])
+        views.append((d_sa[a:b], d_lcp[a + j:b + j + 1], ln[a:b], st[a:b], offs2[a + j:b + j + 1],
+                      starts[o0:max(o1, o0 + 1)]))
+
+    def per_string():
+        for v_sa, v_lcp, v_ln, v_st, v_off, v_starts in views:
+            r, _ = lr.lr_query_all(ctx, v_sa, None, v_lcp, v_ln, v_st, v_off, v_starts, stream, sync=False)
+            if r != lr.LR_OK:
+                raise lr.LRError(r, "lr_query_all")
+
+    loop_ms = _event_ms(stream, per_string, max(1, reps // 2), warm=1)
+    if lr.lr_device_status(ctx, stream) != lr.LR_OK:
+        raise RuntimeError("batched leg: device error in the per-string loop")
+    lr.lr_destroy(ctx)
+    g = lambda ms: round(total / (ms * 1e-3) / 1e9, 3)
+    return {"workload": "batched mix: %d strings, log-uniform lengths 1Ki-4Mi (seed 4)" % count,
+            "positions": total, "lr_starts": tot, "reps": reps,
+            "batched": {"ms": round(batched_ms, 3), "value": g(batched_ms)},
+            "autotuned": {"ms": round(tuned_ms, 3), "value": g(tuned_ms), "shape_code": code},
+            "captured_plan": {"ms": round(plan_ms, 3), "value": g(plan_ms)},
+            "one_string_per_launch": {"ms": round(loop_ms, 3), "value": g(loop_ms)},
+            "unit": UNIT}
+
+
+def serving_leg(lr, dev, count: int, loads, seed: int = 5):
+    """Poisson arrivals of jobs from the serving pool (lognormal lengths,
+    median 100 Ki, sigma 1, 70% DNA / 30% protein) into the library's serving
+    loop, host buffers in pinned memory, at offered loads that are fractions
+    of the loop's measured saturation throughput; the same arrival traces
+    through a plain loop of one lr_query_all_host per job."""
+    import torch
+
+    import workloads as W
+    text, off, _ = W.serving_mix(count, seed=seed)
+    sa, rank, lcp = W.prep_many(text, off)
+    del text, rank
+    lens = np.diff(off)
+    total = int(off[-1])
+    caps = 3 * lens + 1024
+    coff = np.zeros(count + 1, np.int64)
+    np.cumsum(caps, out=coff[1:])
+    h_sa = torch.from_numpy(sa).pin_memory()
+    h_lcp = torch.from_numpy(lcp).pin_memory()
+    del sa, lcp
+    o_ln = torch.empty(total, dtype=torch.int32).pin_memory()
+    o_st = torch.empty(total, dtype=torch.int32).pin_memory()
+    o_off = torch.empty(total + count, dtype=torch.int64).pin_memory()
+    o_starts = torch.empty(int(coff[-1]), dtype=torch.int32).pin_memory()
+    jobs = []
+    for j in range(count):
+        a, b = int(off[j]), int(off[j + 1])
+        jobs.append((h_sa[a:b], h_lcp[a + j:b + j + 1],
+                     (o_ln[a:b], o_st[a:b], o_off[a + j:b + j + 1], o_starts[int(coff[j]):int(coff[j + 1])])))
+    mean_len = total / count
+    srv = lr.Server(dev.index, max_batch_positions=1 << 25, slots=4, max_inflight=2, batch_window_us=1000)
+
+    def run_ours(arrivals):
+        srv.stats(reset=True)
+        t0 = time.perf_counter()
+        ids = []
+        for (j_sa, j_lcp, out), t in zip(jobs, arrivals):
+            while True:
+                dt = t0 + t - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+            ids.append(srv.submit(j_lcp, sa=j_sa, out=out))
+        bad = 0
+        for i in ids:
+            r = srv.wait(i, timeout_ms=600000)[0]
+            bad += r != lr.LR_OK
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        if bad:
+            raise RuntimeError("serving leg: %d jobs failed" % bad)
+        return {"p50_ms": round(st["p50_us"] / 1e3, 3), "p99_ms": round(st["p99_us"] / 1e3, 3),
+                "value": round(total / wall / 1e9, 3), "batches": st["batches"], "jobs": count}
+
+    ctx = lr.lr_create(dev.index)
+    stream = torch.cuda.current_stream(dev)
+
+    def run_plain(arrivals):
+        lat = []
+        t0 = time.perf_counter()
+        for (j_sa, j_lcp, out), t in zip(jobs, arrivals):
+            while True:
+                dt = t0 + t - time.perf_counter()
+                if dt <= 0:
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+            r, _ = lr.lr_query_all_host(ctx, j_sa, None, j_lcp, out[0], out[1], out[2], out[3], stream)
+            if r != lr.LR_OK:
+                raise lr.LRError(r, "lr_query_all_host")
+            lat.append(time.perf_counter() - (t0 + t))
+        wall = time.perf_counter() - t0
+        lat = np.array(lat) * 1e3
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "value": round(total / wall / 1e9, 3)}
+
+    zero = np.zeros(count)
+    run_ours(zero)                                   # warm-up: slots, starts buffers
+    sat = run_ours(zero)
+    run_plain(zero[:8])
+    plain_sat = run_plain(zero)
+    rng = np.random.default_rng(seed)
+    sweep = []
+    for load in loads:
+        lam = load * sat["value"] * 1e9 / mean_len   # jobs per second
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=count))
+        sweep.append({"offered_load": load, "ours": run_ours(arrivals), "one_job_per_call": run_plain(arrivals)})
+    srv.close()
+    lr.lr_destroy(ctx)
+    mid = min(sweep, key=lambda e: abs(e["offered_load"] - 0.6))
+    return {"workload": "serving pool: %d jobs, lognormal lengths (median 100Ki, sigma 1, 1Ki-16Mi), "
+                        "70%% DNA / 30%% protein (seed %d), Poisson arrivals" % (count, seed),
+            "positions": total, "unit": UNIT, "timing": "wall clock, submit to results in pinned host memory",
+            "saturation": sat["value"], "one_job_per_call_saturation": plain_sat["value"],
+            "p50_ms": mid["ours"]["p50_ms"], "p99_ms": mid["ours"]["p99_ms"], "at_offered_load": mid["offered_load"],
+            "sweep": sweep}
+
+
 # --------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -297,6 +482,15 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     lr.lr_destroy(ctx)
+    step = phase_avg = None
+    del d_sa, d_rank, d_lcp, ln, st, off, starts
+    torch.cuda.empty_cache()
+    batched = serving = None
+    if rank == 0 and args.batched_count > 0:
+        batched = batched_leg(lr, dev, stream, args.batched_count, max(3, min(args.steps, 10)))
+        torch.cuda.empty_cache()
+    if rank == 0 and args.serving_jobs > 0:
+        serving = serving_leg(lr, dev, args.serving_jobs, [float(x) for x in args.serving_loads.split(",")])
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -348,6 +542,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8},
             "gpu_launches": launches,
             "clocks": clk,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -394,6 +590,11 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="shrink the workload (same seed); default full size")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--batched-count", type=int, default=512,
+                    help="strings of the batched leg (4096 = the full batched mix; 0 = skip)")
+    ap.add_argument("--serving-jobs", type=int, default=2000, help="jobs in the serving pool (0 = skip)")
+    ap.add_argument("--serving-loads", default="0.2,0.4,0.6,0.8,1.0,1.2",
+                    help="offered loads, as fractions of the serving loop's saturation throughput")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

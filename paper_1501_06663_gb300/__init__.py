@@ -439,20 +439,28 @@ class Server:
         self.handle = lr_server_start(c)
         self._jobs = {}
 
-    def submit(self, lcp, sa=None, rank=None, capacity: int | None = None, pinned: bool = False):
-        """Queues one job; returns its id (raises LRError on LR_ERR_BUSY / NOMEM / ARG)."""
+    def submit(self, lcp, sa=None, rank=None, capacity: int | None = None, pinned: bool = False, out=None):
+        """Queues one job; returns its id (raises LRError on LR_ERR_BUSY / NOMEM / ARG).
+
+        `out` = (lr_len, lr_start, offsets, starts) host arrays to fill
+        instead of newly allocated ones (capacity = len(starts)).
+        """
         import numpy as np
         n = int(len(sa) if sa is not None else len(rank))
-        cap = 4 * n + 1024 if capacity is None else int(capacity)
-        if pinned:
-            import torch
-            outs = (torch.empty(n, dtype=torch.int32, pin_memory=True),
-                    torch.empty(n, dtype=torch.int32, pin_memory=True),
-                    torch.empty(n + 1, dtype=torch.int64, pin_memory=True),
-                    torch.empty(max(cap, 1), dtype=torch.int32, pin_memory=True))
+        if out is not None:
+            outs = tuple(out)
+            cap = int(len(outs[3]))
         else:
-            outs = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n + 1, np.int64),
-                    np.empty(max(cap, 1), np.int32))
+            cap = 4 * n + 1024 if capacity is None else int(capacity)
+            if pinned:
+                import torch
+                outs = (torch.empty(n, dtype=torch.int32, pin_memory=True),
+                        torch.empty(n, dtype=torch.int32, pin_memory=True),
+                        torch.empty(n + 1, dtype=torch.int64, pin_memory=True),
+                        torch.empty(max(cap, 1), dtype=torch.int32, pin_memory=True))
+            else:
+                outs = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n + 1, np.int64),
+                        np.empty(max(cap, 1), np.int32))
         job = Job(_ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), _ptr(outs[3]),
                   cap)
         st, jid = lr_server_submit(self.handle, job)
