@@ -162,6 +162,23 @@ def load_workload(name: str, n: int | None, ws: int, rank: int):
     return w
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest x over all ranks (x itself with one rank).  The tensor lives
+    on `device` (CUDA for NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, n: int, ms: float) -> float:
+    """Gpositions/s of ws replicas of an n-position query whose slowest rank took ms."""
+    return ws * n / (ms * 1e-3) / 1e9
+
+
 def cpu_oracle_rate(w, target_s: float, seed: int = 0):
     """Algorithm 3 (the oracle as it stands) over a contiguous block of positions."""
     import oracle
@@ -428,10 +445,7 @@ def run_ours(args):
     dstat = lr.lr_device_status(ctx, stream)
     if dstat != lr.LR_OK:
         raise lr.LRError(dstat, "device status after the timed steps")
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # per-phase durations (CUDA events on the launching stream, recorded by the library)
     def phase_avg(**kw):
@@ -477,10 +491,7 @@ def run_ours(args):
         if s != lr.LR_OK or tot2 != total:
             raise lr.LRError(s, "lr_query_all_host")
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
     lr.lr_destroy(ctx)
     step = phase_avg = None
     del d_sa, d_rank, d_lcp, ln, st, off, starts
@@ -510,7 +521,7 @@ def run_ours(args):
         # compulsory bytes of the whole query: inputs read once, outputs written once
         path_bytes = 4.0 * n + 4.0 * (n + 1) + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
         path_achieved = path_bytes / (ms * 1e-3) / 1e9
-        value = ws * n / (ms * 1e-3) / 1e9
+        value = whole_job_rate(ws, n, ms)
         rate, block, a0, dt = cpu_oracle_rate(w, args.cpu_seconds)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
@@ -531,13 +542,13 @@ def run_ours(args):
                               "algorithmic_bytes_per_step": path_bytes},
             "kernel_ms": {nm: round(p, 4) for nm, p in zip(names, per)},
             "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
-                                  "value": round(ws * n / (gather_ms * 1e-3) / 1e9, 3),
+                                  "value": round(whole_job_rate(ws, n, gather_ms), 3),
                                   "kernel_ms": {nm: round(p, 4) for nm, p in
                                                 zip(["gather_llr", "cover"], per_gather)}},
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
                                        "[%d, %d) of the same workload, %.1f s single-threaded" % (a0, a0 + block, dt)},
-            "e2e": {"value": round(ws * n / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "e2e": {"value": round(whole_job_rate(ws, n, e2e_ms), 3), "unit": UNIT,
                     "h2d_bytes_per_step": 4 * n + 4 * (n + 1),   # sa + lcp
                     "d2h_bytes_per_step": 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8},
             "gpu_launches": launches,
