@@ -71,6 +71,8 @@ def _bind(lib):
     lib.oracle_lr_at.restype = i64
     lib.oracle_brute.argtypes = [vp, i64, vp, vp, vp, vp, i64]
     lib.oracle_brute.restype = i64
+    lib.oracle_walk_counts.argtypes = [vp, vp, i64, vp, vp]
+    lib.oracle_walk_counts.restype = i64
     return lib
 
 
@@ -191,6 +193,17 @@ def lr_at(rank, lcp, ks):
         raise ValueError("sample position out of range")
     nk = int(ks.size)
     return _csr_call(_L().oracle_lr_at, nk, (_p(rank), _p(lcp), n, _p(ks), nk), 4 * nk)
+
+
+def walk_counts(rank, lcp):
+    """Table 2's walk statistics per position: (alpha, beta, m) with alpha[k]
+    the raw LLR's and beta[k] the compact LLR's covering k (the steps of the
+    walks of Algorithms 1 and 2 that meet a covering LLR), m = |LLRc|."""
+    rank, lcp, n = _check_inputs(rank, lcp)
+    alpha = np.empty(n, np.int32)
+    beta = np.empty(n, np.int32)
+    m = _L().oracle_walk_counts(_p(rank), _p(lcp), n, _p(alpha), _p(beta))
+    return alpha, beta, int(m)
 
 
 def brute(text):

@@ -35,3 +35,30 @@ def lr_all(s: bytes):
         best = max(j - i + 1 for (i, j) in cover)
         out.append((best, sorted(i for (i, j) in cover if j - i + 1 == best)))
     return out
+
+
+def llr_lengths(s: bytes):
+    """|LLR_i| for every i: the length of the longest repeat that starts at i
+    (Sec. 3.1), by growing S[i..j] while it still occurs elsewhere."""
+    n = len(s)
+    out = []
+    for i in range(n):
+        j = i
+        while j < n and is_repeat(s, i, j):
+            j += 1
+        out.append(j - i)
+    return out
+
+
+def covering_counts(s: bytes):
+    """Per position k: (number of LLR's covering k, number of useful ones).
+
+    An LLR is useless when its interval lies inside another LLR's interval
+    (Sec. 3.2); the averages of the two counts are the alpha and beta of
+    Table 2."""
+    L = llr_lengths(s)
+    iv = [(i, i + L[i] - 1) for i in range(len(s)) if L[i] > 0]
+    useful = [(a, b) for (a, b) in iv if not any((c, d) != (a, b) and c <= a and b <= d for (c, d) in iv)]
+    alpha = [sum(1 for (a, b) in iv if a <= k <= b) for k in range(len(s))]
+    beta = [sum(1 for (a, b) in useful if a <= k <= b) for k in range(len(s))]
+    return alpha, beta

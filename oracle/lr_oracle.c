@@ -220,6 +220,43 @@ int64_t oracle_lr_all_compact(const int32_t* rank, const int32_t* lcp, int64_t n
 }
 
 /*
+ * Walk statistics of Table 2, per position k:
+ *   alpha[k] = the raw LLR's that Algorithm 1's leftward walk from k meets
+ *              and that cover k (the walk stops at the first that does not);
+ *   beta[k]  = the compact LLR's that Algorithm 2's rightward walk from the
+ *              binary-search result meets and that cover k.
+ * Lemma 1 of the paper and the statement of Algorithm 2 call their averages
+ * alpha and beta: the number of LLR's (raw, compact) covering a position.
+ * Returns the size of LLRc.
+ */
+int64_t oracle_walk_counts(const int32_t* rank, const int32_t* lcp, int64_t n, int32_t* alpha, int32_t* beta) {
+    int32_t* llrr = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t* cs = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    oracle_llr_raw(rank, lcp, n, llrr);
+    int64_t size = oracle_compact(rank, lcp, n, cs, cl);
+    for (int64_t k = 0; k < n; ++k) {
+        int32_t a = 0;
+        for (int64_t i = k; i >= 0; --i) {
+            if (i + llrr[i] - 1 < k) break;
+            ++a;
+        }
+        int32_t b = 0;
+        int64_t start = first_cover(cs, cl, size, k);
+        if (start != -1) {
+            for (int64_t i = start; i < size; ++i) {
+                if (!(cs[i] <= k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;
+                ++b;
+            }
+        }
+        alpha[k] = a;
+        beta[k] = b;
+    }
+    free(llrr); free(cs); free(cl);
+    return size;
+}
+
+/*
  * Algorithm 3 for a sample of positions only (for spot checks on strings too
  * long to run in full): for each ks[q], the two leftward walks over the raw
  * LLR array, with LLRr[i] computed on demand by Lemma 1.  Returns the total

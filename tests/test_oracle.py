@@ -240,3 +240,55 @@ def test_invariants_on_workloads(name, n):
             if len(sub) == ell + 1:
                 first = s.find(sub)
                 assert s.find(sub, first + 1) == -1
+
+
+# ---------------------------------------------------------------- walk statistics (Table 2)
+
+def test_walk_counts_match_definition():
+    """alpha / beta per position against intervals built from the string alone."""
+    rng = np.random.default_rng(77)
+    for trial in range(120):
+        n = int(rng.integers(1, 36))
+        s = _random_string(rng, n)
+        sa, rank, lcp = _prep(s)
+        alpha, beta, m = oracle.walk_counts(rank, lcp)
+        a2, b2 = definition.covering_counts(s)
+        assert alpha.tolist() == a2, s
+        assert beta.tolist() == b2, s
+        assert m == len(oracle.compact(rank, lcp)[0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 300])
+def test_walk_counts_closed_forms(n):
+    # a^n (n >= 2): LLR_0 = S[0..n-2] and, for i >= 1, LLR_i = S[i..n-1] (the
+    # whole suffix recurs one position to the left); the useful ones are
+    # LLR_0 and LLR_1
+    sa, rank, lcp = _prep(b"a" * n)
+    alpha, beta, m = oracle.walk_counts(rank, lcp)
+    if n == 1:
+        want_a, want_b, want_m = [0], [0], 0
+    else:
+        want_a = [1] + [k + 1 for k in range(1, n - 1)] + [n - 1]
+        want_b = [1] + [2] * (n - 2) + [1]
+        want_m = 2
+    assert alpha.tolist() == want_a and beta.tolist() == want_b
+    assert m == want_m
+    # all symbols distinct: no repeat, no LLR
+    s = bytes(range(1, min(n, 250) + 1))
+    sa, rank, lcp = _prep(s)
+    alpha, beta, m = oracle.walk_counts(rank, lcp)
+    assert not alpha.any() and not beta.any() and m == 0
+
+
+@pytest.mark.parametrize("name,n", [("dna_64m", 1 << 16), ("english_256m", 1 << 16)])
+def test_walk_count_sums(name, n):
+    """Every LLR covers exactly its length in positions: sum(alpha) = sum of
+    |LLR_i|, sum(beta) = sum of the compact lengths."""
+    w = W.single(name, n=n)
+    alpha, beta, m = oracle.walk_counts(w.rank, w.lcp)
+    L = oracle.llr_raw(w.rank, w.lcp)
+    cs, cl = oracle.compact(w.rank, w.lcp)
+    assert int(alpha.sum()) == int(L.astype(np.int64).sum())
+    assert int(beta.sum()) == int(cl.astype(np.int64).sum())
+    assert m == len(cs)
+    assert np.all(beta <= alpha) and np.array_equal(beta == 0, alpha == 0)

@@ -38,6 +38,10 @@ MUTANTS = [
      "if (!(cs[i] < k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                else if (cl[i] > length) length"),
     ("brute diagonal shifted", "run = (s[i] == s[i + d]) ? run + 1 : 0;", "run = (s[i] == s[i + d - 1]) ? run + 1 : 0;"),
     ("brute ignores the later suffix", "if (run > maxrep[i + d]) maxrep[i + d] = run;", "(void)0;"),
+    ("alpha counts the breaking step", "if (i + llrr[i] - 1 < k) break;\n            ++a;",
+     "if (i + llrr[i] - 1 < k) { ++a; break; }\n            ++a;"),
+    ("beta walk stops one early", "if (!(cs[i] <= k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;",
+     "if (!(cs[i] < k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;"),
 ]
 
 
@@ -66,6 +70,9 @@ def _pins_pass() -> bool:
                     assert np.array_equal(a, b)
             for st, ln in (oracle.lr_leftmost_raw(rank, lcp), oracle.lr_leftmost_compact(rank, lcp)):
                 assert np.array_equal(st, want[1]) and np.array_equal(ln, want[0])
+        T.test_walk_counts_match_definition()
+        for n in (2, 7):
+            T.test_walk_counts_closed_forms(n)
         return True
     except AssertionError:
         return False
