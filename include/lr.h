@@ -133,6 +133,39 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
                             int64_t* h_total);
 
 /*
+ * The raw-LLR variant (Sec. 3.1, Algorithms 1 and 3; the paper's GPU
+ * kernels K_LLRr and K_rawwalk of Sec. 4.1): no compaction; every position
+ * walks left over the raw LLR array LLRr while the LLR's it meets cover it.
+ * The results are exactly those of lr_query_all / lr_query_leftmost; the
+ * cost is the sum of the walk lengths, about alpha per position (Table 2),
+ * which the paper compares against the compact array.  Takes rank (text
+ * order) and lcp only; arguments, outputs and errors as lr_query_all /
+ * lr_query_leftmost.
+ */
+lr_status lr_query_all_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp,
+                           int32_t n, int32_t* d_lr_len, int32_t* d_lr_start,
+                           int64_t* d_offsets, int32_t* d_starts, int64_t starts_capacity, int64_t* h_total);
+lr_status lr_query_leftmost_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp,
+                                int32_t n, int32_t* d_lr_start, int32_t* d_lr_len);
+
+/*
+ * Walk statistics of Table 2 on the device: alpha_k, the number of raw LLR's
+ * covering position k (the steps of Algorithm 1's walk that meet a covering
+ * LLR), and beta_k, the number of compact (useful, Sec. 3.2) LLR's covering
+ * k.  d_alpha / d_beta (n entries each) receive the per-position values when
+ * non-NULL; *h_summary receives n, m = |LLRc|, the sums, minima and maxima
+ * (the call waits for `stream`).  Errors as lr_query_all.
+ */
+typedef struct {
+    int64_t n, m;
+    int64_t alpha_sum, beta_sum;
+    int32_t alpha_min, alpha_max, beta_min, beta_max;
+} lr_walk_summary;
+
+lr_status lr_walk_stats(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                        int32_t* d_alpha, int32_t* d_beta, lr_walk_summary* h_summary);
+
+/*
  * Batched query: many strings of uneven length in one set of launches over
  * a flattened position space (the strings back to back).  String j owns the
  * flattened positions [d_off[j], d_off[j+1]); its own (local, 0-based) sa or

@@ -35,6 +35,7 @@ EXPORTED = (
     "lr_plan_create", "lr_plan_launch", "lr_plan_result", "lr_plan_destroy",
     "lr_server_start", "lr_server_submit", "lr_server_poll", "lr_server_wait", "lr_server_cancel",
     "lr_server_stats_get", "lr_server_stop",
+    "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats",
 )
 
 LR_JOB_QUEUED, LR_JOB_ADMITTED, LR_JOB_RUNNING, LR_JOB_DONE, LR_JOB_CANCELLED = range(5)
@@ -70,6 +71,13 @@ class ServerStats(ctypes.Structure):
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
                 ("max_us", ctypes.c_double), ("slots", ctypes.c_int32), ("slot_positions", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class WalkSummary(ctypes.Structure):
+    """lr_walk_summary: Table 2's walk statistics of one string."""
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("alpha_sum", ctypes.c_int64),
+                ("beta_sum", ctypes.c_int64), ("alpha_min", ctypes.c_int32), ("alpha_max", ctypes.c_int32),
+                ("beta_min", ctypes.c_int32), ("beta_max", ctypes.c_int32)]
 
 
 class LRError(RuntimeError):
@@ -120,6 +128,9 @@ def load(path: str | None = None):
     lib.lr_server_cancel.argtypes = [vp, i64]
     lib.lr_server_stats_get.argtypes = [vp, i32, ctypes.POINTER(ServerStats)]
     lib.lr_server_stop.argtypes = [vp]
+    lib.lr_query_all_raw.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.lr_query_leftmost_raw.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+    lib.lr_walk_stats.argtypes = [vp, vp, vp, vp, i32, vp, vp, ctypes.POINTER(WalkSummary)]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -306,6 +317,29 @@ def lr_plan_destroy(plan) -> None:
     _check(load().lr_plan_destroy(plan), "lr_plan_destroy")
 
 
+def lr_query_all_raw(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
+    """The raw-LLR variant (no compaction) of lr_query_all.  Returns (status, total or None)."""
+    n = int(rank.numel())
+    cap = int(starts.numel()) if starts is not None else 0
+    tot = ctypes.c_int64(-1)
+    st = load().lr_query_all_raw(ctx, _stream(stream), _ptr(rank), _ptr(lcp), n, _ptr(lr_len), _ptr(lr_start),
+                                 _ptr(offsets), _ptr(starts), cap, ctypes.byref(tot) if sync else None)
+    return st, (tot.value if sync else None)
+
+
+def lr_query_leftmost_raw(ctx, rank, lcp, lr_start, lr_len, stream=None) -> int:
+    return load().lr_query_leftmost_raw(ctx, _stream(stream), _ptr(rank), _ptr(lcp), int(rank.numel()),
+                                        _ptr(lr_start), _ptr(lr_len))
+
+
+def lr_walk_stats(ctx, rank, lcp, alpha=None, beta=None, stream=None) -> dict:
+    """Table 2's alpha / beta statistics (per position into alpha / beta when given)."""
+    out = WalkSummary()
+    _check(load().lr_walk_stats(ctx, _stream(stream), _ptr(rank), _ptr(lcp), int(rank.numel()), _ptr(alpha),
+                                _ptr(beta), ctypes.byref(out)), "lr_walk_stats")
+    return {name: getattr(out, name) for name, _ in WalkSummary._fields_}
+
+
 def lr_server_start(cfg: ServerConfig | None = None):
     h = ctypes.c_void_p()
     _check(load().lr_server_start(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(h)),
@@ -398,6 +432,41 @@ class Context:
             st, total = lr_query_all(self.handle, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream)
         _check(st, "lr_query_all")
         return lr_len, lr_start, offsets, starts[:total]
+
+    def query_all_raw(self, lcp, rank, capacity: int | None = None, stream=None):
+        """The raw-LLR variant: (lr_len, lr_start, offsets, starts[:total]) from rank and lcp."""
+        import torch
+        n = int(rank.numel())
+        dev = rank.device
+        lr_len = torch.empty(n, dtype=torch.int32, device=dev)
+        lr_start = torch.empty(n, dtype=torch.int32, device=dev)
+        offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        cap = 2 * n + 1024 if capacity is None else int(capacity)
+        starts = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        st, total = lr_query_all_raw(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+        if st == LR_ERR_CAPACITY:
+            starts = torch.empty(total, dtype=torch.int32, device=dev)
+            st, total = lr_query_all_raw(self.handle, rank, lcp, lr_len, lr_start, offsets, starts, stream)
+        _check(st, "lr_query_all_raw")
+        return lr_len, lr_start, offsets, starts[:total]
+
+    def query_leftmost_raw(self, lcp, rank, stream=None):
+        import torch
+        n = int(rank.numel())
+        lr_start = torch.empty(n, dtype=torch.int32, device=rank.device)
+        lr_len = torch.empty(n, dtype=torch.int32, device=rank.device)
+        _check(lr_query_leftmost_raw(self.handle, rank, lcp, lr_start, lr_len, stream), "lr_query_leftmost_raw")
+        _check(lr_device_status(self.handle, stream), "lr_query_leftmost_raw (device)")
+        return lr_start, lr_len
+
+    def walk_stats(self, lcp, rank, per_position: bool = False, stream=None):
+        """Table 2's statistics; with per_position also the alpha and beta arrays."""
+        import torch
+        n = int(rank.numel())
+        a = torch.empty(n, dtype=torch.int32, device=rank.device) if per_position else None
+        b = torch.empty(n, dtype=torch.int32, device=rank.device) if per_position else None
+        summary = lr_walk_stats(self.handle, rank, lcp, a, b, stream)
+        return (summary, a, b) if per_position else summary
 
     def query_batch(self, off, lcp, sa=None, rank=None, capacity: int | None = None, stream=None):
         """Batched all-LR query over a flattened string table (device tensors).

@@ -420,6 +420,76 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_sa
     return tot > starts_capacity ? LR_ERR_CAPACITY : LR_OK;
 }
 
+lr_status lr_query_all_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                           int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
+                           int64_t starts_capacity, int64_t* h_total) {
+    if (!ctx || !d_rank || !d_lcp || !d_lr_len || !d_lr_start || !d_offsets) return LR_ERR_ARG;
+    if (starts_capacity < 0 || (starts_capacity > 0 && !d_starts)) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr::Scratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    cudaError_t e = lr::launch_raw_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
+                                         starts_capacity, true, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    ctx->last_launches = 2;
+    if (!h_total) return LR_OK;
+    st = sync_total(ctx, (cudaStream_t)stream, d_offsets + n, h_total);
+    if (st != LR_OK) return st;
+    return (*h_total > starts_capacity) ? LR_ERR_CAPACITY : LR_OK;
+}
+
+lr_status lr_query_leftmost_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp,
+                                int32_t n, int32_t* d_lr_start, int32_t* d_lr_len) {
+    if (!ctx || !d_rank || !d_lcp || !d_lr_start || !d_lr_len) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr::Scratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    cudaError_t e = lr::launch_raw_query(d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    ctx->last_launches = 2;
+    return LR_OK;
+}
+
+lr_status lr_walk_stats(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
+                        int32_t* d_alpha, int32_t* d_beta, lr_walk_summary* h_summary) {
+    if (!ctx || !d_rank || !d_lcp || !h_summary) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr::Scratch s;
+    lr_status st = get_scratch(ctx, n, &s);
+    if (st != LR_OK) return st;
+    // the six result words live in the context's 256-byte error block, after the error word
+    unsigned long long* d_stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(ctx->d_err) + 64);
+    cudaStream_t strm = (cudaStream_t)stream;
+    cudaError_t e = lr::launch_walk_stats(d_rank, d_lcp, n, s, d_alpha, d_beta, d_stats, strm);
+    unsigned long long hs[4] = {0, 0, 0, 0};
+    int32_t m = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, strm);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, s.tile_cbase + s.ntiles, 4, cudaMemcpyDeviceToHost, strm);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    ctx->last_launches = 4;
+    st = sync_total(ctx, strm, nullptr, nullptr);
+    if (st != LR_OK) return st;
+    const int32_t* w = reinterpret_cast<const int32_t*>(hs + 2);
+    h_summary->n = n;
+    h_summary->m = m;
+    h_summary->alpha_sum = (int64_t)hs[0];
+    h_summary->beta_sum = (int64_t)hs[1];
+    h_summary->alpha_min = w[0];
+    h_summary->alpha_max = w[1];
+    h_summary->beta_min = w[2];
+    h_summary->beta_max = w[3];
+    return LR_OK;
+}
+
 namespace {
 
 lr_status check_batch(const lr_batch_desc* b) {

@@ -103,6 +103,14 @@ void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_star
 
 cudaError_t configure_kernels();
 
+// The raw-LLR variant (Algorithms 1 and 3 on the GPU, no compaction) and the
+// walk statistics of Table 2 (lr_raw.cu).  Both keep LLRr in s.lbig.
+cudaError_t launch_raw_query(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, int32_t* lr_len,
+                             int32_t* lr_start, int64_t* offsets, int32_t* starts, long long capacity, bool all,
+                             cudaStream_t stream);
+cudaError_t launch_walk_stats(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, int32_t* alpha,
+                              int32_t* beta, unsigned long long* stats, cudaStream_t stream);
+
 // Scratch management (lr_api.cu): bytes of a scratch block for n positions,
 // and the carving of such a block (laid out for cap_n >= n) into `s`.
 size_t scratch_size(long long n);
