@@ -475,6 +475,16 @@ def run_ours(args):
     gather_ms = g0.elapsed_time(g1) / gsteps
     per_gather = phase_avg(sa=None, rank=d_rank)
 
+    # Table 2's walk statistics and the raw-LLR variant (no compaction), for comparison
+    walk = lr.lr_walk_stats(ctx, d_rank, d_lcp, stream=stream)
+    raw = None
+    if walk["alpha_sum"] <= 64 * n:                  # the raw walks cost about alpha per position
+        raw_ms = _event_ms(stream, lambda: lr.lr_query_all_raw(ctx, d_rank, d_lcp, ln, st, off, starts, stream,
+                                                               sync=False), 3, warm=1)
+        if lr.lr_device_status(ctx, stream) != lr.LR_OK:
+            raise RuntimeError("raw-LLR variant: device error")
+        raw = {"ms_per_step": round(raw_ms, 4), "value": round(whole_job_rate(ws, n, raw_ms), 3)}
+
     # e2e through the host-buffer entry point, pinned host memory
     h_sa = torch.from_numpy(w.sa).pin_memory()
     h_lcp = torch.from_numpy(w.lcp).pin_memory()
@@ -541,6 +551,10 @@ def run_ours(args):
                               "frac": round(path_achieved / peak, 4), "peak_kind": peak_kind,
                               "algorithmic_bytes_per_step": path_bytes},
             "kernel_ms": {nm: round(p, 4) for nm, p in zip(names, per)},
+            "walk_steps": {"alpha": round(walk["alpha_sum"] / n, 3), "alpha_max": walk["alpha_max"],
+                           "beta": round(walk["beta_sum"] / n, 3), "beta_max": walk["beta_max"],
+                           "definition": "LLR's covering a position, raw (alpha) and useful (beta), Table 2"},
+            "raw_llr_variant": raw,
             "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
                                   "value": round(whole_job_rate(ws, n, gather_ms), 3),
                                   "kernel_ms": {nm: round(p, 4) for nm, p in
