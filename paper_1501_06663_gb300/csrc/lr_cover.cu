@@ -55,6 +55,7 @@ struct __align__(16) CoverSmem {
     int32_t spre[kChunks];           // exclusive prefix popcounts of the bitmap words
     int32_t epre[kChunks];
     int32_t chunk[kChunks];          // run totals of the tie counts
+    unsigned rt[Cfg<TP>::kWarps][6][kWarp];   // per warp: range-max levels 0..4, equal-length masks
     long long tile;
     long long obase;
     int32_t lo;
@@ -222,16 +223,82 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             for (int32_t v = lw; v <= hi; ++v) step(__ldg(gce + v) - __ldg(gcs + v) + 1, v);
         }
     };
-    // per run: longest length, index of its leftmost holder, number of ties
-    int32_t best[kChunksPerWarp], vbest[kChunksPerWarp], cnt[kChunksPerWarp];
+    // Per run of 32 positions: the windows of its lanes lie inside one range
+    // [U0, U1] of at most a few dozen entries (both window ends only move
+    // right).  When it has at most 32 entries, lane j holds entry U0 + j and
+    // the warp builds a range-maximum table over the keys (length << 5 |
+    // 31 - j) in five shuffle levels, plus each lane's mask of equal lengths
+    // (match.any); a window's longest length and leftmost holder are then
+    // two table reads and its holders one mask, with no per-lane loop (whose
+    // cost in a warp would be the longest window of its 32 lanes).  Other
+    // runs take the walk of best_of.
+    //
+    // Per run the lane keeps best[] (longest length) and pk[] packed:
+    //   staged tiles:  bits 0..12 leftmost holder v (0x1fff: none); bit 31
+    //                  clear: bits 13..30 = holders as a mask from v (bit 0 =
+    //                  v); bit 31 set: bits 13..30 = number of holders;
+    //   other tiles:   the number of holders.
+    constexpr uint32_t kNone = 0x1fffu;
+    int32_t best[kChunksPerWarp];
+    uint32_t pk[kChunksPerWarp];
+    unsigned (*RT)[kWarp] = sm.rt[warp];
 #pragma unroll
     for (int q = 0; q < kChunksPerWarp; ++q) {
         const int c = q * kWarps + warp;
-        int32_t lw, hi, b, vb, ct;
+        int32_t lw, hi;
         window(c, lw, hi);
-        best_of(lw, hi, b, vb, ct);
-        best[q] = b; vbest[q] = vb; cnt[q] = ct;
+        const int32_t U0 = __shfl_sync(kFull, lw, 0);
+        const int32_t usz = __shfl_sync(kFull, hi, kWarp - 1) - U0 + 1;
+        bool fast = staged && usz <= kWarp;                       // warp-uniform
+        int32_t len_l = 0;
+        if (fast) {
+            len_l = ((int)lane < usz) ? SCL[U0 + (int)lane] : 0;
+            fast = !__any_sync(kFull, len_l >= (1 << 27));       // keys need length < 2^27
+        }
+        if (fast) {
+            unsigned key = ((int)lane < usz) ? (((unsigned)len_l << 5) | (31u - lane)) : 0u;
+            RT[0][lane] = key;
+            RT[5][lane] = __match_any_sync(kFull, len_l);
+#pragma unroll
+            for (int l = 1; l <= 4; ++l) {
+                const unsigned o = __shfl_down_sync(kFull, key, 1u << (l - 1));
+                key = key > o ? key : o;
+                RT[l][lane] = key;
+            }
+            __syncwarp();
+            int32_t b = 0;
+            uint32_t p = kNone;
+            if (lw <= hi) {
+                const int l0 = lw - U0, h0 = hi - U0;
+                int lv = 31 - __clz(h0 - l0 + 1);
+                lv = lv > 4 ? 4 : lv;
+                const unsigned ka = RT[lv][l0], kb = RT[lv][h0 - (1 << lv) + 1];
+                const unsigned kk = ka > kb ? ka : kb;
+                b = (int32_t)(kk >> 5);
+                const int jl = 31 - (int)(kk & 31u);
+                const unsigned range = ((2u << h0) - 1u) & ~((1u << jl) - 1u);
+                const unsigned hold = (RT[5][jl] & range) >> jl;
+                const uint32_t v = (uint32_t)(U0 + jl);
+                p = hold < (1u << 18) ? (v | (hold << 13)) : (v | ((uint32_t)__popc(hold) << 13) | 0x80000000u);
+            }
+            __syncwarp();                                         // before the next run rewrites RT
+            best[q] = b;
+            pk[q] = p;
+        } else {
+            int32_t b, vb, ct;
+            best_of(lw, hi, b, vb, ct);
+            best[q] = b;
+            if (!staged) pk[q] = (uint32_t)ct;
+            else if (ct == 0) pk[q] = kNone;
+            else if (ct == 1) pk[q] = (uint32_t)vb | (1u << 13);
+            else pk[q] = (uint32_t)vb | ((uint32_t)ct << 13) | 0x80000000u;
+        }
     }
+    // holders of run q (the tie count of its position)
+    auto count_of = [&](uint32_t p) -> int32_t {
+        if (!staged) return (int32_t)p;
+        return (p >> 31) ? (int32_t)((p >> 13) & 0x3ffffu) : __popc(p >> 13);
+    };
     int pre[kChunksPerWarp];
     if constexpr (kAll) {
         // CSR offsets: scan of the tie counts within the tile.  Counts are
@@ -240,16 +307,17 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         // later tiles rarely wait for it.
 #pragma unroll
         for (int q = 0; q < kChunksPerWarp; ++q) {
+            const int32_t cq = count_of(pk[q]);
             int incl;
-            if (__any_sync(kFull, cnt[q] > 3)) {
-                incl = warp_incl_scan(cnt[q]);
+            if (__any_sync(kFull, cq > 3)) {
+                incl = warp_incl_scan(cq);
             } else {
                 const unsigned upto = below | (1u << lane);
-                incl = __popc(__ballot_sync(kFull, cnt[q] >= 1) & upto) +
-                       __popc(__ballot_sync(kFull, cnt[q] >= 2) & upto) +
-                       __popc(__ballot_sync(kFull, cnt[q] >= 3) & upto);
+                incl = __popc(__ballot_sync(kFull, cq >= 1) & upto) +
+                       __popc(__ballot_sync(kFull, cq >= 2) & upto) +
+                       __popc(__ballot_sync(kFull, cq >= 3) & upto);
             }
-            pre[q] = incl - cnt[q];
+            pre[q] = incl - cq;
             if (lane == kWarp - 1) sm.chunk[q * kWarps + warp] = incl;
         }
         __syncthreads();
@@ -267,7 +335,18 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         const int32_t k = k0 + c * kWarp + lane;
         if (k < n) {
             __stcs(lr_len + k, best[q]);
-            __stcs(lr_start + k, vbest[q] >= 0 ? start_of(vbest[q]) : -1);
+            int32_t st = -1;
+            if (best[q] > 0) {
+                if (staged) {
+                    st = start_of((int32_t)(pk[q] & kNone));
+                } else {                                          // leftmost holder: first of the window
+                    int32_t lw, hi;
+                    window(c, lw, hi);
+                    for (int32_t v = lw; v <= hi; ++v)
+                        if (__ldg(gce + v) - __ldg(gcs + v) + 1 == best[q]) { st = __ldg(gcs + v); break; }
+                }
+            }
+            __stcs(lr_start + k, st);
         }
     }
 
@@ -290,16 +369,23 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             const int32_t k = k0 + c * kWarp + lane;
             long long o = obase + sm.chunk[c] + pre[q];
             if (k < n) __stcs(reinterpret_cast<long long*>(offsets) + k, o);
-            if (cnt[q] == 0) continue;
-            // second walk of Algorithm 4, from the leftmost holder: every
-            // compact LLR of the longest length, ascending; with one holder
-            // (the common case) it is already known
-            if (o < capacity) __stcs(starts + o, start_of(vbest[q]));
-            if (cnt[q] > 1) {
-                ++o;
+            const uint32_t p = pk[q];
+            if (count_of(p) == 0) continue;
+            // the second walk of Algorithm 4: every compact LLR of the
+            // longest length, ascending
+            if (staged && !(p >> 31)) {
+                const int32_t v0 = (int32_t)(p & kNone);
+                unsigned m = p >> 13;
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1u;
+                    if (o < capacity) __stcs(starts + o, start_of(v0 + j));
+                    ++o;
+                }
+            } else {
                 int32_t lw, hi;
                 window(c, lw, hi);
-                for (int32_t v = vbest[q] + 1; v <= hi; ++v) {
+                for (int32_t v = staged ? (int32_t)(p & kNone) : lw; v <= hi; ++v) {
                     const int32_t len = staged ? SCL[v] : __ldg(gce + v) - __ldg(gcs + v) + 1;
                     if (len == best[q]) {
                         if (o < capacity) __stcs(starts + o, start_of(v));
