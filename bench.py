@@ -485,6 +485,25 @@ def run_ours(args):
             raise RuntimeError("raw-LLR variant: device error")
         raw = {"ms_per_step": round(raw_ms, 4), "value": round(whole_job_rate(ws, n, raw_ms), 3)}
 
+    # the step before the query: sa / rank / lcp built on the GPU from the text
+    # (prefix doubling), checked against the host prep
+    d_text = torch.from_numpy(w.text).to(dev)
+    b_sa = torch.empty(n, dtype=torch.int32, device=dev)
+    b_rank = torch.empty(n, dtype=torch.int32, device=dev)
+    b_lcp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    s_b, rounds = lr.lr_build_arrays(ctx, d_text, b_sa, b_rank, b_lcp, stream)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    if s_b != lr.LR_OK:
+        raise lr.LRError(s_b, "lr_build_arrays")
+    index_build = {"ms": round(build_ms, 1), "value": round(n / (build_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+                   "doubling_rounds": rounds,
+                   "equal_to_host_prep": bool(torch.equal(b_sa, d_sa) and torch.equal(b_rank, d_rank)
+                                              and torch.equal(b_lcp, d_lcp))}
+    del d_text, b_sa, b_rank, b_lcp
+    torch.cuda.empty_cache()
+
     # e2e through the host-buffer entry point, pinned host memory
     h_sa = torch.from_numpy(w.sa).pin_memory()
     h_lcp = torch.from_numpy(w.lcp).pin_memory()
@@ -555,6 +574,7 @@ def run_ours(args):
                            "beta": round(walk["beta_sum"] / n, 3), "beta_max": walk["beta_max"],
                            "definition": "LLR's covering a position, raw (alpha) and useful (beta), Table 2"},
             "raw_llr_variant": raw,
+            "index_build": index_build,
             "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
                                   "value": round(whole_job_rate(ws, n, gather_ms), 3),
                                   "kernel_ms": {nm: round(p, 4) for nm, p in

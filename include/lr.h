@@ -133,6 +133,24 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
                             int64_t* h_total);
 
 /*
+ * The step before the query: sa, rank and lcp of a device text, built on the
+ * GPU.  The paper builds these arrays on the host and notes they could be
+ * built in parallel on the GPU by prefix doubling (Sec. 4); this call does
+ * that: radix sorts of the first 7 symbols, then of (rank(i), rank(i + h))
+ * pairs for h = 7, 14, 28, ... until all ranks differ, and the lcp of sa
+ * neighbours by binary lifting over the ranks of every round.
+ *
+ * d_text: n bytes (any values); outputs in the layout the queries take:
+ * d_sa and d_rank n entries, d_lcp n + 1 (lcp[0] = lcp[n] = 0).  The work
+ * memory, about (32 + 4 R) bytes per position for R doubling rounds (R is
+ * about log2 of the longest repeat / 7, plus 2), is allocated by the call
+ * and freed before it returns (LR_ERR_NOMEM when it does not fit).  Waits
+ * for `stream`; *rounds (may be NULL) receives R.
+ */
+lr_status lr_build_arrays(lr_ctx* ctx, lr_stream_t stream, const uint8_t* d_text, int32_t n,
+                          int32_t* d_sa, int32_t* d_rank, int32_t* d_lcp, int32_t* rounds);
+
+/*
  * The raw-LLR variant (Sec. 3.1, Algorithms 1 and 3; the paper's GPU
  * kernels K_LLRr and K_rawwalk of Sec. 4.1): no compaction; every position
  * walks left over the raw LLR array LLRr while the LLR's it meets cover it.

@@ -35,7 +35,7 @@ EXPORTED = (
     "lr_plan_create", "lr_plan_launch", "lr_plan_result", "lr_plan_destroy",
     "lr_server_start", "lr_server_submit", "lr_server_poll", "lr_server_wait", "lr_server_cancel",
     "lr_server_stats_get", "lr_server_stop",
-    "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats",
+    "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats", "lr_build_arrays",
 )
 
 LR_JOB_QUEUED, LR_JOB_ADMITTED, LR_JOB_RUNNING, LR_JOB_DONE, LR_JOB_CANCELLED = range(5)
@@ -131,6 +131,7 @@ def load(path: str | None = None):
     lib.lr_query_all_raw.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.lr_query_leftmost_raw.argtypes = [vp, vp, vp, vp, i32, vp, vp]
     lib.lr_walk_stats.argtypes = [vp, vp, vp, vp, i32, vp, vp, ctypes.POINTER(WalkSummary)]
+    lib.lr_build_arrays.argtypes = [vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -317,6 +318,14 @@ def lr_plan_destroy(plan) -> None:
     _check(load().lr_plan_destroy(plan), "lr_plan_destroy")
 
 
+def lr_build_arrays(ctx, text, sa, rank, lcp, stream=None):
+    """sa, rank, lcp of a device uint8 text, built on the GPU.  Returns (status, rounds)."""
+    r = ctypes.c_int32(0)
+    st = load().lr_build_arrays(ctx, _stream(stream), _ptr(text), int(text.numel()), _ptr(sa), _ptr(rank),
+                                _ptr(lcp), ctypes.byref(r))
+    return st, r.value
+
+
 def lr_query_all_raw(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
     """The raw-LLR variant (no compaction) of lr_query_all.  Returns (status, total or None)."""
     n = int(rank.numel())
@@ -432,6 +441,17 @@ class Context:
             st, total = lr_query_all(self.handle, sa, rank, lcp, lr_len, lr_start, offsets, starts, stream)
         _check(st, "lr_query_all")
         return lr_len, lr_start, offsets, starts[:total]
+
+    def build_arrays(self, text, stream=None):
+        """(sa, rank, lcp) of a device uint8 text, built on the GPU by prefix doubling."""
+        import torch
+        n = int(text.numel())
+        sa = torch.empty(n, dtype=torch.int32, device=text.device)
+        rank = torch.empty(n, dtype=torch.int32, device=text.device)
+        lcp = torch.empty(n + 1, dtype=torch.int32, device=text.device)
+        st, _ = lr_build_arrays(self.handle, text, sa, rank, lcp, stream)
+        _check(st, "lr_build_arrays")
+        return sa, rank, lcp
 
     def query_all_raw(self, lcp, rank, capacity: int | None = None, stream=None):
         """The raw-LLR variant: (lr_len, lr_start, offsets, starts[:total]) from rank and lcp."""

@@ -420,6 +420,20 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_sa
     return tot > starts_capacity ? LR_ERR_CAPACITY : LR_OK;
 }
 
+lr_status lr_build_arrays(lr_ctx* ctx, lr_stream_t stream, const uint8_t* d_text, int32_t n, int32_t* d_sa,
+                          int32_t* d_rank, int32_t* d_lcp, int32_t* rounds) {
+    if (!ctx || !d_text || !d_sa || !d_rank || !d_lcp) return LR_ERR_ARG;
+    if (check_n(n) != LR_OK) return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    int r = 0;
+    cudaError_t e = lr::build_arrays(d_text, n, d_sa, d_rank, d_lcp, (cudaStream_t)stream, &r);
+    if (e == cudaErrorMemoryAllocation) return LR_ERR_NOMEM;
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if (rounds) *rounds = r;
+    return LR_OK;
+}
+
 lr_status lr_query_all_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,
                            int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
                            int64_t starts_capacity, int64_t* h_total) {

@@ -111,6 +111,11 @@ cudaError_t launch_raw_query(const int32_t* rank, const int32_t* lcp, int32_t n,
 cudaError_t launch_walk_stats(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, int32_t* alpha,
                               int32_t* beta, unsigned long long* stats, cudaStream_t stream);
 
+// Suffix array, rank and lcp of a device text by prefix doubling
+// (lr_index.cu); allocates and frees its own work memory.
+cudaError_t build_arrays(const uint8_t* text, int32_t n, int32_t* sa, int32_t* rank, int32_t* lcp,
+                         cudaStream_t stream, int* rounds_out);
+
 // Scratch management (lr_api.cu): bytes of a scratch block for n positions,
 // and the carving of such a block (laid out for cap_n >= n) into `s`.
 size_t scratch_size(long long n);

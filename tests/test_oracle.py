@@ -292,3 +292,32 @@ def test_walk_count_sums(name, n):
     assert int(beta.sum()) == int(cl.astype(np.int64).sum())
     assert m == len(cs)
     assert np.all(beta <= alpha) and np.array_equal(beta == 0, alpha == 0)
+
+
+# ---------------------------------------------------------------- the prep (SA, rank, lcp) itself
+
+def test_prep_matches_naive_suffix_sort():
+    """The host prep's sa / rank / lcp (the inputs every test feeds both
+    sides, and the expected arrays of the GPU builder) against sorting the
+    suffixes as byte strings and comparing neighbours symbol by symbol."""
+    rng = np.random.default_rng(5)
+    cases = [b"mississippi", b"a", b"aaaaaaa", b"\x00\x00\x01\x00\xff\xff\x00"]
+    for _ in range(200):
+        n = int(rng.integers(1, 80))
+        sigma = int(rng.integers(1, 5))
+        alphabet = rng.choice(256, size=sigma, replace=False)
+        cases.append(bytes(alphabet[rng.integers(0, sigma, n)].astype(np.uint8)))
+    for s in cases:
+        sa, rank, lcp = W.prep(np.frombuffer(s, np.uint8))
+        n = len(s)
+        want_sa = sorted(range(n), key=lambda i: s[i:])
+        assert sa.tolist() == want_sa, s
+        assert np.array_equal(rank[sa], np.arange(n))
+        want_lcp = [0] * (n + 1)
+        for r in range(1, n):
+            a, b = s[want_sa[r - 1]:], s[want_sa[r]:]
+            m = 0
+            while m < min(len(a), len(b)) and a[m] == b[m]:
+                m += 1
+            want_lcp[r] = m
+        assert lcp.tolist() == want_lcp, s
