@@ -42,14 +42,15 @@ struct Cfg {
     static constexpr int kWarps = kThr / kWarp;
     static constexpr int kChunks = kTileC / kWarp;
     static constexpr int kChunksPerWarp = kChunks / kWarps;
-    static constexpr int kMinBlocks = TP == 1 ? 5 : 3;
+    static constexpr int kMinBlocks = TP == 1 ? 5 : 4;
+    static constexpr int kCap = kTileC + 128;     // staged entries: the tile's own and a carry
 };
 
 template <int TP>
 struct __align__(16) CoverSmem {
     static constexpr int kChunks = Cfg<TP>::kChunks;
-    int32_t cs[kCoverCap];           // window range LLRc[lo, cb1): starts
-    int32_t cl[kCoverCap];           //                             lengths
+    int32_t cs[Cfg<TP>::kCap];       // window range LLRc[lo, cb1): starts
+    int32_t cl[Cfg<TP>::kCap];       //                             lengths
     unsigned smap[kChunks];          // bit x: an entry of the tile starts at k0 + x
     unsigned emap[kChunks];          // bit x: an entry of the range ends at k0 + x
     int32_t spre[kChunks];           // exclusive prefix popcounts of the bitmap words
@@ -124,7 +125,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     constexpr int32_t kSpec = 64;
     const int32_t sbase = cb0 > kSpec ? cb0 - kSpec : 0;
     const int32_t MS = cb1 - sbase;
-    const bool fits = MS <= kCoverCap;
+    const bool fits = MS <= Cfg<TP>::kCap;
     if (fits) {
         for (int i = tid; i < MS; i += kCoverThreads) {
             const int32_t cs = __ldg(s.cstart + sbase + i), ce = __ldg(s.cend + sbase + i);

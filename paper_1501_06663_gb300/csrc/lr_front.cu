@@ -254,7 +254,18 @@ __device__ __forceinline__ PartSmem part_smem(unsigned char* raw, int nb) {
     return p;
 }
 
-size_t part_smem_bytes(int nb) { return (size_t)(3 * nb + 1) * 4 + (size_t)kPartRound * 6; }
+// Bulk-copy staging of a level-1 round: sa[r0, r0 + kPartRound) and
+// lcp[r0, r0 + kPartRound + 4) (16-byte multiples), at a 16-byte-aligned
+// offset after the counters; it overlaps the stage area, which is written
+// only after every thread has read its entries.
+constexpr int kPartLoadBytes = kPartRound * 4 + (kPartRound + 4) * 4;
+__host__ __device__ inline size_t part_load_offset(int nb) { return ((size_t)(3 * nb + 1) * 4 + 15) & ~(size_t)15; }
+
+size_t part_smem_bytes(int nb) {
+    const size_t a = (size_t)(3 * nb + 1) * 4 + (size_t)kPartRound * 6;
+    const size_t b = part_load_offset(nb) + kPartLoadBytes;
+    return a > b ? a : b;
+}
 
 // Exclusive scan of hist[0..nb) into loff[0..nb] by the whole CTA
 // (kPartThreads threads, nb <= 2 * kPartThreads), and one global atomic per
@@ -295,12 +306,26 @@ __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned
 // bucket's predecessor).
 template <bool kBatch>
 __global__ void __launch_bounds__(kPartThreads, 2)
-k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs) {
+k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs, int tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long load_bar;
     const int nb = (int)s.nsupers;                    // <= 2048
     const PartSmem P = part_smem(smem_raw, nb);
-    for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
     const long long r0 = (long long)blockIdx.x * kPartRound;
+    // Full rounds of a single string (16-byte-aligned inputs) arrive by two
+    // bulk copies issued before anything else; the last round and batches
+    // load per thread.
+    const bool bulk = !kBatch && tma && r0 + kPartRound + 4 <= (long long)n + 1;
+    const int32_t* Ssa = reinterpret_cast<const int32_t*>(smem_raw + part_load_offset(nb));
+    const int32_t* Slcp = Ssa + kPartRound;
+    if (bulk && threadIdx.x == 0) {
+        mbar_init(&load_bar, 1);
+        mbar_fence_init();
+        mbar_arrive_tx(&load_bar, (unsigned)kPartLoadBytes);
+        bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
+        bulk_g2s(const_cast<int32_t*>(Slcp), lcp + r0, (kPartRound + 4) * 4, &load_bar);
+    }
+    for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
     __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
     SegView sv{};
     if constexpr (kBatch) sv.stage(segs, s, r0, (r0 + kPartRound < n) ? r0 + kPartRound : n, seg_sh);
@@ -313,10 +338,25 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
     uint32_t p[kPartPer];
     int32_t L[kPartPer];
     long long hint = kBatch ? sv.j0 : 0;
+    bool landed = true;
+    if (bulk && !mbar_wait(&load_bar, 0)) {           // the copies never landed: report, load nothing
+        landed = false;
+        if (threadIdx.x == 0) report(s, kErrTimeout);
+    }
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const long long r = r0 + (long long)j * kPartThreads + threadIdx.x;
-        if (r < n) {
+        if (bulk) {
+            const int x = j * kPartThreads + (int)threadIdx.x;
+            if (!landed) { p[j] = 0xffffffffu; L[j] = 0; continue; }
+            uint32_t pl = (uint32_t)Ssa[x];
+            const int32_t a = Slcp[x], c = Slcp[x + 1];
+            int32_t Lj = a > c ? a : c;
+            if (pl >= (uint32_t)n) { bad = 1; pl = 0xffffffffu; }
+            else if (Lj < 0 || (long long)Lj > (long long)n - pl) { bad = 1; Lj = 0; }
+            p[j] = pl;
+            L[j] = Lj;
+        } else if (r < n) {
             uint32_t pl = (uint32_t)__ldcs(sa + r);
             long long base = 0, nj = n, lidx = r;
             if constexpr (kBatch) {
@@ -396,18 +436,31 @@ k_part2(int32_t n, Scratch s) {
     __syncthreads();
     const uint32_t i0 = (uint32_t)q * kPartRound;
     if (i0 >= fill) return;                             // uniform over the CTA
-    const uint32_t* src = s.ent1 + ((size_t)b1 << kSuperLog);
+    // the chunk's kPartRound entries (always inside the super-bucket's
+    // region; those past `fill` are ignored) arrive by one bulk copy
+    __shared__ unsigned long long load_bar;
+    const uint32_t* src = s.ent1 + ((size_t)b1 << kSuperLog) + i0;
+    const uint32_t* Sent = reinterpret_cast<const uint32_t*>(smem_raw + part_load_offset(kSubPerSuper));
+    if (threadIdx.x == 0) {
+        mbar_init(&load_bar, 1);
+        mbar_fence_init();
+        mbar_arrive_tx(&load_bar, kPartRound * 4u);
+        bulk_g2s(const_cast<uint32_t*>(Sent), src, kPartRound * 4u, &load_bar);
+    }
+    __syncthreads();
+    const bool landed = mbar_wait(&load_bar, 0);
+    if (!landed && threadIdx.x == 0) report(s, kErrTimeout);
     uint32_t ent[kPartPer], key[kPartPer];
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
-        ent[j] = (i < fill) ? __ldcs(src + i) : 0xffffffffu;
+        ent[j] = (landed && i < fill) ? Sent[j * kPartThreads + threadIdx.x] : 0xffffffffu;
     }
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
         key[j] = 0xffffffffu;
-        if (i >= fill) continue;
+        if (i >= fill || !landed) continue;
         const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
         const uint32_t b2 = low20 >> kBucketLog;
         ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
@@ -557,10 +610,13 @@ size_t bucket_smem_bytes() { return (size_t)kBucket * 2 + (size_t)(kBucket / kWa
 void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
                       cudaStream_t stream) {
     const unsigned g1 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
-    if (segs.num > 0)
-        k_part1<true><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs);
-    else
-        k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs);
+    if (segs.num > 0) {
+        k_part1<true><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, 0);
+    } else {
+        // bulk copies need 16-byte-aligned sources
+        const int tma = (((uintptr_t)sa | (uintptr_t)lcp) & 15u) == 0 ? 1 : 0;
+        k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, tma);
+    }
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
     k_part2<<<g2, kPartThreads, part_smem_bytes(kSubPerSuper), stream>>>(n, s);
 }

@@ -11,7 +11,6 @@ namespace lr {
 constexpr int kTile = 2048;          // positions per tile (one CTA)
 constexpr int kThreads = 256;        // threads per tile CTA
 // Tiles of the cover kernel: kTile x (1 or 2) positions, kThreads x the same threads.
-constexpr int kCoverCap = 4096;      // compact LLR's a cover tile stages in shared memory
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
 // position, into super-buckets of 2^20 and then buckets of 2^16 positions.
