@@ -526,15 +526,26 @@ k_bucket_llr(int32_t n, Scratch s) {
     const uint32_t fill = __ldcg(s.cursor2 + (size_t)b * kCursorStride);
     unsigned bad = fill != (uint32_t)cnt;
     const int nent = (int)(fill < (uint32_t)cnt ? fill : (uint32_t)cnt);
-    for (int i = tid; i < nent; i += kBucketThreads) {
-        const uint32_t e = __ldcs(ent + i);
-        const uint32_t low = e >> 17, f = e & kEsc17;
-        if (low < (uint32_t)cnt) {
-            sL[low] = (uint16_t)(f == kEsc17 ? 0xffffu : f);
-            const unsigned bit = 1u << (low & 31);
-            if (atomicOr(cmask + (low >> 5), bit) & bit) bad = 1;
-        } else {
-            bad = 1;
+    // eight loads in flight per thread before any of them is used
+    constexpr int kUnroll = 8;
+    for (int i0 = 0; i0 < nent; i0 += kBucketThreads * kUnroll) {
+        uint32_t e[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kBucketThreads + tid;
+            e[u] = (i < nent) ? __ldcs(ent + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (i0 + u * kBucketThreads + tid >= nent) continue;
+            const uint32_t low = e[u] >> 17, f = e[u] & kEsc17;
+            if (low < (uint32_t)cnt) {
+                sL[low] = (uint16_t)(f == kEsc17 ? 0xffffu : f);
+                const unsigned bit = 1u << (low & 31);
+                if (atomicOr(cmask + (low >> 5), bit) & bit) bad = 1;
+            } else {
+                bad = 1;
+            }
         }
     }
     if (bad) report(s, kErrInput);
