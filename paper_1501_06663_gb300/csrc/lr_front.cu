@@ -267,6 +267,9 @@ size_t part_smem_bytes(int nb) {
     return a > b ? a : b;
 }
 
+// level 2 loads per thread: counters and stage area only
+size_t part2_smem_bytes() { return (size_t)(3 * kSubPerSuper + 1) * 4 + (size_t)kPartRound * 6; }
+
 // Exclusive scan of hist[0..nb) into loff[0..nb] by the whole CTA
 // (kPartThreads threads, nb <= 2 * kPartThreads), and one global atomic per
 // non-empty bucket to reserve the round's room: base[b] = old cursor.
@@ -436,31 +439,18 @@ k_part2(int32_t n, Scratch s) {
     __syncthreads();
     const uint32_t i0 = (uint32_t)q * kPartRound;
     if (i0 >= fill) return;                             // uniform over the CTA
-    // the chunk's kPartRound entries (always inside the super-bucket's
-    // region; those past `fill` are ignored) arrive by one bulk copy
-    __shared__ unsigned long long load_bar;
-    const uint32_t* src = s.ent1 + ((size_t)b1 << kSuperLog) + i0;
-    const uint32_t* Sent = reinterpret_cast<const uint32_t*>(smem_raw + part_load_offset(kSubPerSuper));
-    if (threadIdx.x == 0) {
-        mbar_init(&load_bar, 1);
-        mbar_fence_init();
-        mbar_arrive_tx(&load_bar, kPartRound * 4u);
-        bulk_g2s(const_cast<uint32_t*>(Sent), src, kPartRound * 4u, &load_bar);
-    }
-    __syncthreads();
-    const bool landed = mbar_wait(&load_bar, 0);
-    if (!landed && threadIdx.x == 0) report(s, kErrTimeout);
+    const uint32_t* src = s.ent1 + ((size_t)b1 << kSuperLog);
     uint32_t ent[kPartPer], key[kPartPer];
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
-        ent[j] = (landed && i < fill) ? Sent[j * kPartThreads + threadIdx.x] : 0xffffffffu;
+        ent[j] = (i < fill) ? __ldcs(src + i) : 0xffffffffu;
     }
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
         key[j] = 0xffffffffu;
-        if (i >= fill || !landed) continue;
+        if (i >= fill) continue;
         const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
         const uint32_t b2 = low20 >> kBucketLog;
         ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
@@ -629,7 +619,7 @@ void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Sc
         k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, tma);
     }
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
-    k_part2<<<g2, kPartThreads, part_smem_bytes(kSubPerSuper), stream>>>(n, s);
+    k_part2<<<g2, kPartThreads, part2_smem_bytes(), stream>>>(n, s);
 }
 
 void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream) {
@@ -645,7 +635,7 @@ cudaError_t configure_front() {
     e = cudaFuncSetAttribute(k_part1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_part2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)part_smem_bytes(kSubPerSuper));
+                                (int)part2_smem_bytes());
 }
 
 }  // namespace lr
