@@ -169,10 +169,38 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
         if (!kBatch && tile == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
     }
     hint = kBatch ? sv.j0 : 0;
+    if constexpr (kBatch) {
 #pragma unroll
-    for (int j = 0; j < kTile / kThreads; ++j) {
-        const int x = j * kThreads + tid;
-        Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
+        for (int j = 0; j < kTile / kThreads; ++j) {
+            const int x = j * kThreads + tid;
+            Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
+        }
+    } else {
+        // all rank loads, then all lcp loads, then the lengths: every load
+        // of a thread is in flight before the first one is used
+        constexpr int kPer = kTile / kThreads;
+        uint32_t r[kPer];
+        int32_t a[kPer], c[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long k = k0 + j * kThreads + tid;
+            r[j] = (k < n) ? (uint32_t)__ldcs(rank + k) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const long long k = k0 + j * kThreads + tid;
+            if (k < n && r[j] >= (uint32_t)n) { bad = 1; r[j] = 0; }
+            a[j] = (k < n) ? __ldg(lcp + r[j]) : 0;
+            c[j] = (k < n) ? __ldg(lcp + r[j] + 1) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int x = j * kThreads + tid;
+            const long long k = k0 + x;
+            int32_t L = a[j] > c[j] ? a[j] : c[j];
+            if (k < n && (L < 0 || (long long)L > (long long)n - k)) { bad = 1; L = 0; }
+            Ls[1 + x] = (k < n) ? L : 0;
+        }
     }
     if (bad) report(s, kErrInput);
     __syncthreads();
