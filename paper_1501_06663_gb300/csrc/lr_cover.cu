@@ -60,6 +60,7 @@ struct __align__(16) CoverSmem {
     long long tile;
     long long obase;
     int32_t lo;
+    int32_t nlow;                    // staged carry candidates that end before the tile
     int32_t ttot;                    // the tile's total of tie counts
 };
 
@@ -107,6 +108,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) sm.tile = atomicAdd(&s.tickets[2], 1u);
     if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
+    if (tid == 0) sm.nlow = 0;
     __syncthreads();
     const long long tile = sm.tile;
     const int32_t k0 = (int32_t)(tile * kCoverTile);         // n < 2^31: positions fit 32 bits
@@ -126,29 +128,38 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     const int32_t sbase = cb0 > kSpec ? cb0 - kSpec : 0;
     const int32_t MS = cb1 - sbase;
     const bool fits = MS <= Cfg<TP>::kCap;
+    // One pass over the staged entries: lengths, the two bitmaps (entries of
+    // [sbase, lo) end before k0, so they set no bit), and the number of
+    // staged carry candidates that end before k0: ends increase, so they
+    // are a prefix and lo = sbase + that number.
+    const int32_t nspec = cb0 - sbase;
     if (fits) {
-        for (int i = tid; i < MS; i += kCoverThreads) {
-            const int32_t cs = __ldg(s.cstart + sbase + i), ce = __ldg(s.cend + sbase + i);
-            sm.cs[i] = cs; sm.cl[i] = ce;                        // ends for now, lengths below
+        for (int i0 = 0; i0 < MS; i0 += kCoverThreads) {
+            const int i = i0 + tid;
+            bool low = false;
+            if (i < MS) {
+                const int32_t cs = __ldg(s.cstart + sbase + i), ce = __ldg(s.cend + sbase + i);
+                sm.cs[i] = cs;
+                sm.cl[i] = ce - cs + 1;
+                const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
+                if (i >= nspec && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
+                if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
+                low = i < nspec && ce < k0;
+            }
+            const unsigned m = __ballot_sync(kFull, low);
+            if (lane == 0 && m) atomicAdd(&sm.nlow, __popc(m));
         }
     }
     __syncthreads();
-    if (warp == 0) {
-        int32_t t = cb0;
-        bool done = false;
-        if (fits) {                                              // scan the staged speculative part
-            while (t > sbase) {
-                const int32_t idx = t - 1 - lane;
-                const bool reach = idx >= sbase && sm.cl[idx - sbase] >= k0;
-                const unsigned m = __ballot_sync(kFull, reach);
-                if (m == kFull) { t -= kWarp; continue; }
-                t -= __ffs(~m) - 1;
-                done = true;
-                break;
-            }
-            if (t == 0) done = true;
-        }
-        if (!done) {                                             // carry longer than staged: scan LLRc
+    // staged unless every staged candidate reaches k0 with more LLRc before
+    // them: then the carry may be longer, and it is found in LLRc itself
+    const int32_t nlow = sm.nlow;
+    const bool staged = fits && !(sbase > 0 && nlow == 0);
+    int32_t lo = sbase + nlow;
+    if (!staged) {
+        if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
+        if (warp == 0) {
+            int32_t t = cb0;
             while (t > 0) {
                 const int32_t idx = t - 1 - lane;
                 const bool reach = idx >= 0 && __ldg(s.cend + idx) >= k0;
@@ -157,32 +168,22 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                 t -= __ffs(~m) - 1;
                 break;
             }
+            if (lane == 0) sm.lo = t;
         }
-        if (lane == 0) sm.lo = t;
-    }
-    __syncthreads();
-    const int32_t lo = sm.lo;
-    const int32_t C = cb0 - lo, M = cb1 - lo;
-    // staged: window entry v sits at sm.cs/cl[v + shift]
-    const bool staged = fits && lo >= sbase;
-    const int32_t shift = staged ? lo - sbase : 0;
-    if (staged) {
-        for (int i = tid; i < M; i += kCoverThreads) {
-            const int32_t cs = sm.cs[shift + i], ce = sm.cl[shift + i];
-            sm.cl[shift + i] = ce - cs + 1;
-            const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
-            if (i >= C && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
-            if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
-        }
-    } else {
-        for (int i = tid; i < M; i += kCoverThreads) {
+        __syncthreads();
+        lo = sm.lo;
+        const int32_t Cg = cb0 - lo, Mg = cb1 - lo;
+        for (int i = tid; i < Mg; i += kCoverThreads) {
             const int32_t cs = __ldg(s.cstart + lo + i), ce = __ldg(s.cend + lo + i);
             const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
-            if (i >= C && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
+            if (i >= Cg && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
             if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
         }
+        __syncthreads();
     }
-    __syncthreads();
+    const int32_t C = cb0 - lo;
+    // staged: window entry v sits at sm.cs/cl[v + shift]
+    const int32_t shift = staged ? lo - sbase : 0;
     if (warp == 0) popc_prefix<kChunks>(sm.smap, sm.spre);
     if (warp == 1) popc_prefix<kChunks>(sm.emap, sm.epre);
     __syncthreads();
