@@ -152,6 +152,24 @@ def test_dna_iid_1m_full(ctx, front):
 
 
 @pytest.mark.parametrize("front", FRONTS)
+def test_binary_iid_full(ctx, front):
+    """Binary i.i.d. text: nearly every position starts a useful LLR and
+    windows are wide, so runs of 32 positions often span more than 32 compact
+    LLR's (the cover's looped path) and ties are frequent and spread."""
+    text = W.iid(1 << 24, b"ab", 77)
+    sa, rank, lcp = W.prep(text)
+    want = oracle.lr_all_raw(rank, lcp)
+    _assert_csr_equal(_gpu_all(ctx, sa, rank, lcp, front), want, "binary iid")
+    # some positions have holders 18 or more compact LLR's apart (the cover
+    # then lists them by walking the window instead of from a bit mask)
+    _, _, off, starts = want
+    cs, _ = oracle.compact(rank, lcp)
+    multi = np.nonzero(np.diff(off) > 1)[0]
+    span = np.searchsorted(cs, starts[off[multi + 1] - 1]) - np.searchsorted(cs, starts[off[multi]])
+    assert int(span.max()) >= 18
+
+
+@pytest.mark.parametrize("front", FRONTS)
 def test_dna_planted_4m_full(ctx, front):
     w = W.single("dna_64m", n=4 * W.MI)
     _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp), w.name)
