@@ -17,7 +17,8 @@
  * The string itself is not needed.  Lemma 1 gives the length of the
  * left-bounded longest repeat at i as L_i = max(lcp[rank[i]], lcp[rank[i]+1]),
  * which read in rank order is L_{sa[r]} = max(lcp[r], lcp[r+1]).  A query
- * takes sa or rank (at least one; sa wins when both are given):
+ * takes sa or rank (at least one; when both are given, sa is used unless
+ * lr_autotune chose the rank front end for queries of that size):
  *   - with sa, the lengths are computed in rank order (sa and lcp read
  *     once, coalesced) and radix-partitioned back to text order;
  *   - with rank only, each position gathers its two lcp words, the paper's
@@ -212,13 +213,14 @@ lr_status lr_batch_query_all(lr_ctx* ctx, lr_stream_t stream, const lr_batch_des
                              int64_t* h_total);
 
 /*
- * Autotuning.  Kernel shape choices (the cover tile: 2048 or 4096
+ * Autotuning.  Kernel shape choices (the cover tile: 2048, 4096 or 8192
  * positions; the front end, when both sa and rank are given) are timed on
  * the given batch (a single string is a batch with num = 1) and the fastest
  * is remembered in the context for batches of the same shape class (total
  * size and mean string length, both rounded to powers of two).  Later
  * queries of that class use it.  *choice receives the chosen shape code
- * (bit 0: 4096-position cover tile; bit 1: rank-gather front end).  The
+ * (bit 0: 4096-position cover tile, bit 2: 8192-position cover tile, neither:
+ * 2048; bit 1: rank-gather front end).  The
  * outputs are overwritten.  lr_autotune_save / _load write and read the
  * remembered choices as a small text file (one "class code" pair per line).
  */

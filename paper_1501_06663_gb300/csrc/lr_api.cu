@@ -163,9 +163,13 @@ int shape_class(long long total, long long num) {
 
 lr::Shape shape_of(int code) {
     lr::Shape sh;
-    sh.cover_tiles_per = (code & 1) ? 2 : 1;
+    sh.cover_tiles_per = (code & 4) ? 4 : ((code & 1) ? 2 : 1);
     return sh;
 }
+
+// Shape codes lr_autotune tries: cover tiles of 2048, 4096 or 8192
+// positions (bit 0 / bit 2), each with either front end (bit 1).
+constexpr int kShapeCodes[] = {0, 1, 4, 2, 3, 6};
 
 // The tuned shape code for a batch (default: 4096-position cover tiles,
 // rank-order front end).
@@ -333,7 +337,9 @@ lr_status lr_query_leftmost(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa
     lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
-    const lr::Shape shape = shape_of(tuned_code(ctx, n, 1));
+    const int code = tuned_code(ctx, n, 1);
+    const lr::Shape shape = shape_of(code);
+    if ((code & 2) && d_rank) d_sa = nullptr;                  // tuned: the rank-gather front end
     cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, nullptr, nullptr, 0, false,
                                      (cudaStream_t)stream, &ctx->last_launches, &ctx->events, lr::Segs{nullptr, 0},
                                      shape);
@@ -351,7 +357,9 @@ lr_status lr_query_all(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_sa, con
     lr::Scratch s;
     lr_status st = get_scratch(ctx, n, &s);
     if (st != LR_OK) return st;
-    const lr::Shape shape = shape_of(tuned_code(ctx, n, 1));
+    const int code = tuned_code(ctx, n, 1);
+    const lr::Shape shape = shape_of(code);
+    if ((code & 2) && d_rank) d_sa = nullptr;                  // tuned: the rank-gather front end
     cudaError_t e = lr::launch_query(d_sa, d_rank, d_lcp, n, s, d_lr_len, d_lr_start, d_offsets, d_starts,
                                      starts_capacity, true, (cudaStream_t)stream, &ctx->last_launches, &ctx->events,
                                      lr::Segs{nullptr, 0}, shape);
@@ -559,7 +567,7 @@ lr_status lr_autotune(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batc
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ctx, cudaErrorUnknown); }
     int best = -1;
     float best_ms = 0.f;
-    for (int code = 0; code < 4; ++code) {
+    for (int code : kShapeCodes) {
         const bool front_rank = code & 2;
         if (front_rank && (!batch->d_rank || !batch->d_sa)) continue;   // only a choice when both are given
         float acc = 0.f;
@@ -601,7 +609,7 @@ lr_status lr_autotune_load(lr_ctx* ctx, const char* path) {
     if (!f) return LR_ERR_ARG;
     int cls = 0, code = 0;
     while (std::fscanf(f, "%d %d", &cls, &code) == 2)
-        if (code >= 0 && code < 4) ctx->tuned[cls] = code;
+        if (code >= 0 && code < 8 && (code & 5) != 5) ctx->tuned[cls] = code;
     std::fclose(f);
     return LR_OK;
 }

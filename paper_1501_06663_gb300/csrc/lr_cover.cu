@@ -42,7 +42,7 @@ struct Cfg {
     static constexpr int kWarps = kThr / kWarp;
     static constexpr int kChunks = kTileC / kWarp;
     static constexpr int kChunksPerWarp = kChunks / kWarps;
-    static constexpr int kMinBlocks = TP == 1 ? 5 : 4;
+    static constexpr int kMinBlocks = TP == 1 ? 5 : (TP == 2 ? 4 : 2);
     static constexpr int kCap = kTileC + 128;     // staged entries: the tile's own and a carry
 };
 
@@ -104,7 +104,8 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     constexpr int kWarps = Cfg<TP>::kWarps;
     constexpr int kChunks = Cfg<TP>::kChunks;
     constexpr int kChunksPerWarp = Cfg<TP>::kChunksPerWarp;
-    __shared__ CoverSmem<TP> sm;
+    extern __shared__ __align__(16) unsigned char cover_smem[];
+    CoverSmem<TP>& sm = *reinterpret_cast<CoverSmem<TP>*>(cover_smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) sm.tile = atomicAdd(&s.tickets[2], 1u);
     if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
@@ -399,20 +400,50 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     }
 }
 
+namespace {
+
+template <bool kAll, int TP>
+void launch_cover_t(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
+                    int32_t* starts, long long capacity, cudaStream_t stream) {
+    const unsigned grid = (unsigned)num_cover_tiles(n, TP);
+    k_cover<kAll, TP><<<grid, Cfg<TP>::kThr, sizeof(CoverSmem<TP>), stream>>>(n, s, lr_len, lr_start, offsets, starts,
+                                                                              capacity);
+}
+
+template <int TP>
+cudaError_t set_cover_smem() {
+    cudaError_t e = cudaFuncSetAttribute(k_cover<true, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(CoverSmem<TP>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_cover<false, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(CoverSmem<TP>));
+    return e;
+}
+
+}  // namespace
+
+cudaError_t configure_cover() {
+    cudaError_t e = set_cover_smem<1>();
+    if (e == cudaSuccess) e = set_cover_smem<2>();
+    if (e == cudaSuccess) e = set_cover_smem<4>();
+    return e;
+}
+
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
                   int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream) {
-    if (tiles_per == 1) {
-        const unsigned grid = (unsigned)num_cover_tiles(n, 1);
-        if (all)
-            k_cover<true, 1><<<grid, Cfg<1>::kThr, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
-        else
-            k_cover<false, 1><<<grid, Cfg<1>::kThr, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
-    } else {
-        const unsigned grid = (unsigned)num_cover_tiles(n, 2);
-        if (all)
-            k_cover<true, 2><<<grid, Cfg<2>::kThr, 0, stream>>>(n, s, lr_len, lr_start, offsets, starts, capacity);
-        else
-            k_cover<false, 2><<<grid, Cfg<2>::kThr, 0, stream>>>(n, s, lr_len, lr_start, nullptr, nullptr, 0);
+    if (!all) { offsets = nullptr; starts = nullptr; capacity = 0; }
+    switch (tiles_per) {
+        case 1:
+            if (all) launch_cover_t<true, 1>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
+            else launch_cover_t<false, 1>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
+            break;
+        case 4:
+            if (all) launch_cover_t<true, 4>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
+            else launch_cover_t<false, 4>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
+            break;
+        default:
+            if (all) launch_cover_t<true, 2>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
+            else launch_cover_t<false, 2>(n, s, lr_len, lr_start, offsets, starts, capacity, stream);
     }
 }
 

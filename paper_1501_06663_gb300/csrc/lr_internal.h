@@ -80,7 +80,7 @@ constexpr int kSegCap = 1024;      // strings per CTA a front end keeps in share
 
 // Kernel shape choices a query can take (picked by lr_autotune_*).
 struct Shape {
-    int cover_tiles_per = 2;       // cover tile = kTile x this (1 or 2)
+    int cover_tiles_per = 2;       // cover tile = kTile x this (1, 2 or 4)
 };
 
 // Launches the whole query on `stream`: the front end (rank-order when sa is

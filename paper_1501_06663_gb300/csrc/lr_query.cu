@@ -8,8 +8,12 @@
 namespace lr {
 
 cudaError_t configure_front();
+cudaError_t configure_cover();
 
-cudaError_t configure_kernels() { return configure_front(); }
+cudaError_t configure_kernels() {
+    cudaError_t e = configure_front();
+    return e == cudaSuccess ? configure_cover() : e;
+}
 
 cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
                          int32_t* lr_len, int32_t* lr_start, int64_t* offsets, int32_t* starts,

@@ -178,7 +178,7 @@ def test_autotune_choice_keeps_results_and_round_trips(ctx, tmp_path):
     desc = P.batch_desc(d_off, d_lcp, sa=d_sa, rank=d_rank)
     outs = _outs(n, 4 * n)
     code = P.lr_autotune(ctx.handle, desc, *outs)
-    assert 0 <= code < 4
+    assert code in (0, 1, 2, 3, 4, 6)
     # every shape gives the same answer: run the tuned one through the normal entry point
     got = ctx.query_batch(d_off, d_lcp, sa=d_sa, rank=d_rank)
     _assert_equal(tuple(t.cpu().numpy() for t in got), want, "tuned code %d" % code)
@@ -244,3 +244,25 @@ def test_plan_reports_capacity(ctx):
         assert np.array_equal(outs[2].cpu().numpy(), want[2])
     finally:
         P.lr_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("code", [0, 1, 4, 2, 3, 6])
+def test_every_shape_code_matches_the_oracle(ctx, code, tmp_path):
+    """Each shape the autotuner can pick (cover tile 2048 / 4096 / 8192,
+    either front end) gives the oracle's answer, single string and batch."""
+    w = W.single("dna_64m", n=700_000)
+    text, off, _ = W.batched_mix(count=24, lo=1024, hi=64 * 1024, seed=13)
+    sa_b, rank_b, lcp_b = _batch(text, off)
+    lg = lambda v: int(v).bit_length() - 1
+    classes = [lg(w.n) * 64 + lg(w.n), lg(off[-1]) * 64 + lg(int(off[-1]) // (off.size - 1))]
+    path = tmp_path / "codes.txt"
+    path.write_text("".join("%d %d\n" % (c, code) for c in classes))
+    c = P.Context(0)
+    try:
+        P.lr_autotune_load(c.handle, str(path))
+        got = tuple(t.cpu().numpy() for t in c.query_all(_dev(w.lcp), sa=_dev(w.sa), rank=_dev(w.rank)))
+        _assert_equal(got, oracle.lr_all_raw(w.rank, w.lcp), "single, code %d" % code)
+        got = tuple(t.cpu().numpy() for t in c.query_batch(_dev(off), _dev(lcp_b), sa=_dev(sa_b), rank=_dev(rank_b)))
+        _assert_equal(got, _expected(off, rank_b, lcp_b), "batch, code %d" % code)
+    finally:
+        c.close()
