@@ -134,22 +134,39 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
                             int64_t* h_total);
 
 /*
- * The step before the query: sa, rank and lcp of a device text, built on the
+ * The step before the query: sa, rank and lcp of device text, built on the
  * GPU.  The paper builds these arrays on the host and notes they could be
- * built in parallel on the GPU by prefix doubling (Sec. 4); this call does
- * that: radix sorts of the first 7 symbols, then of (rank(i), rank(i + h))
- * pairs for h = 7, 14, 28, ... until all ranks differ, and the lcp of sa
- * neighbours by binary lifting over the ranks of every round.
+ * built in parallel on the GPU by prefix doubling (Sec. 4); these calls do
+ * that: radix sorts of (string index, first symbols) keys, then of
+ * (rank(i), rank(i + h)) pairs for doubling h until all ranks differ, and
+ * the lcp of sa neighbours by binary lifting over the ranks of every round.
  *
- * d_text: n bytes (any values); outputs in the layout the queries take:
- * d_sa and d_rank n entries, d_lcp n + 1 (lcp[0] = lcp[n] = 0).  The work
- * memory, about (32 + 4 R) bytes per position for R doubling rounds (R is
- * about log2 of the longest repeat / 7, plus 2), is allocated by the call
- * and freed before it returns (LR_ERR_NOMEM when it does not fit).  Waits
- * for `stream`; *rounds (may be NULL) receives R.
+ * lr_build_arrays: one string, d_text n bytes (any values); outputs in the
+ * layout the queries take: d_sa and d_rank n entries, d_lcp n + 1
+ * (lcp[0] = lcp[n] = 0).
+ * lr_batch_build_arrays: many strings packed back to back, in the layout of
+ * lr_batch_desc: string j = d_text[d_off[j], d_off[j+1]) (empty strings
+ * allowed); its local sa and rank at the same offsets of d_sa / d_rank, its
+ * lcp (n_j + 1 entries) at d_lcp + d_off[j] + j (total + num entries).
+ *
+ * Work memory, about (36 + 4 R) bytes per position for R doubling rounds
+ * (R is about log2 of the longest repeat / 7, plus 2), is kept in the
+ * context and grown on demand (LR_ERR_NOMEM when it does not fit).  Both
+ * calls wait for `stream` (once per round); *rounds (may be NULL) receives R.
+ * An offset table that does not start at 0, end at total or never
+ * decrease is reported as LR_ERR_SENTINEL before any symbol is read.
  */
+typedef struct {
+    int64_t num;                /* number of strings (>= 1) */
+    int64_t total;              /* d_off[num]: total symbols, 0 <= total <= 2^31 - 2 */
+    const int64_t* d_off;       /* num + 1 device offsets, d_off[0] = 0, non-decreasing */
+    const uint8_t* d_text;      /* total bytes */
+} lr_text_batch;
+
 lr_status lr_build_arrays(lr_ctx* ctx, lr_stream_t stream, const uint8_t* d_text, int32_t n,
                           int32_t* d_sa, int32_t* d_rank, int32_t* d_lcp, int32_t* rounds);
+lr_status lr_batch_build_arrays(lr_ctx* ctx, lr_stream_t stream, const lr_text_batch* batch,
+                                int32_t* d_sa, int32_t* d_rank, int32_t* d_lcp, int32_t* rounds);
 
 /*
  * The raw-LLR variant (Sec. 3.1, Algorithms 1 and 3; the paper's GPU

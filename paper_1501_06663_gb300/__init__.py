@@ -35,7 +35,7 @@ EXPORTED = (
     "lr_plan_create", "lr_plan_launch", "lr_plan_result", "lr_plan_destroy",
     "lr_server_start", "lr_server_submit", "lr_server_poll", "lr_server_wait", "lr_server_cancel",
     "lr_server_stats_get", "lr_server_stop",
-    "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats", "lr_build_arrays",
+    "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats", "lr_build_arrays", "lr_batch_build_arrays",
 )
 
 LR_JOB_QUEUED, LR_JOB_ADMITTED, LR_JOB_RUNNING, LR_JOB_DONE, LR_JOB_CANCELLED = range(5)
@@ -71,6 +71,12 @@ class ServerStats(ctypes.Structure):
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
                 ("max_us", ctypes.c_double), ("slots", ctypes.c_int32), ("slot_positions", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64)]
+
+
+class TextBatch(ctypes.Structure):
+    """lr_text_batch: texts packed back to back (see include/lr.h)."""
+    _fields_ = [("num", ctypes.c_int64), ("total", ctypes.c_int64), ("d_off", ctypes.c_void_p),
+                ("d_text", ctypes.c_void_p)]
 
 
 class WalkSummary(ctypes.Structure):
@@ -132,6 +138,7 @@ def load(path: str | None = None):
     lib.lr_query_leftmost_raw.argtypes = [vp, vp, vp, vp, i32, vp, vp]
     lib.lr_walk_stats.argtypes = [vp, vp, vp, vp, i32, vp, vp, ctypes.POINTER(WalkSummary)]
     lib.lr_build_arrays.argtypes = [vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(i32)]
+    lib.lr_batch_build_arrays.argtypes = [vp, vp, ctypes.POINTER(TextBatch), vp, vp, vp, ctypes.POINTER(i32)]
     for name in EXPORTED:
         f = getattr(lib, name)
         if name not in ("lr_status_str", "lr_last_launch_count", "lr_phase_times"):
@@ -326,6 +333,15 @@ def lr_build_arrays(ctx, text, sa, rank, lcp, stream=None):
     return st, r.value
 
 
+def lr_batch_build_arrays(ctx, off, text, sa, rank, lcp, stream=None):
+    """sa, rank, lcp of device uint8 texts packed back to back (off: int64, num + 1).  Returns (status, rounds)."""
+    desc = TextBatch(int(off.numel()) - 1, int(text.numel()), _ptr(off), _ptr(text))
+    r = ctypes.c_int32(0)
+    st = load().lr_batch_build_arrays(ctx, _stream(stream), ctypes.byref(desc), _ptr(sa), _ptr(rank), _ptr(lcp),
+                                      ctypes.byref(r))
+    return st, r.value
+
+
 def lr_query_all_raw(ctx, rank, lcp, lr_len, lr_start, offsets, starts, stream=None, sync=True):
     """The raw-LLR variant (no compaction) of lr_query_all.  Returns (status, total or None)."""
     n = int(rank.numel())
@@ -452,6 +468,18 @@ class Context:
         st, _ = lr_build_arrays(self.handle, text, sa, rank, lcp, stream)
         _check(st, "lr_build_arrays")
         return sa, rank, lcp
+
+    def build_arrays_batch(self, off, text, stream=None):
+        """(sa, rank, lcp) of device uint8 texts packed back to back, in the batched-query layout."""
+        import torch
+        total = int(text.numel())
+        num = int(off.numel()) - 1
+        sa = torch.empty(max(total, 1), dtype=torch.int32, device=text.device)
+        rank = torch.empty(max(total, 1), dtype=torch.int32, device=text.device)
+        lcp = torch.empty(total + num, dtype=torch.int32, device=text.device)
+        st, _ = lr_batch_build_arrays(self.handle, off, text, sa, rank, lcp, stream)
+        _check(st, "lr_batch_build_arrays")
+        return sa[:total], rank[:total], lcp
 
     def query_all_raw(self, lcp, rank, capacity: int | None = None, stream=None):
         """The raw-LLR variant: (lr_len, lr_start, offsets, starts[:total]) from rank and lcp."""

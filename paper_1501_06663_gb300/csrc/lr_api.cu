@@ -27,6 +27,8 @@ struct lr_ctx {
     lr::PhaseEvents events;               // per-kernel timing (off by default)
     bool events_created = false;
     std::map<int, int> tuned;             // shape class -> shape code (lr_autotune)
+    lr::IndexWork index_work;             // work memory of lr_build_arrays / lr_batch_build_arrays
+    int64_t* d_off2 = nullptr;            // {0, n} for single-string builds
 };
 
 struct lr_plan {
@@ -263,6 +265,8 @@ lr_status lr_destroy(lr_ctx* ctx) {
     if (ctx->hostpath) cudaFree(ctx->hostpath);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->index_work.release();
+    if (ctx->d_off2) cudaFree(ctx->d_off2);
     if (ctx->events_created)
         for (int i = 0; i <= lr::kMaxPhases; ++i) cudaEventDestroy(ctx->events.ev[i]);
     delete ctx;
@@ -428,18 +432,64 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream, const int32_t* h_sa
     return tot > starts_capacity ? LR_ERR_CAPACITY : LR_OK;
 }
 
+namespace {
+
+// Grows the context's index work memory to `total` positions (waits for the
+// device when it has to reallocate).
+lr_status index_work_for(lr_ctx* ctx, long long total) {
+    if (ctx->index_work.cap_n >= total && ctx->index_work.base) return LR_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    e = ctx->index_work.alloc(total > 0 ? total : 1, 8);
+    return e == cudaSuccess ? LR_OK : LR_ERR_NOMEM;
+}
+
+lr_status index_status(lr_ctx* ctx, cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return LR_ERR_NOMEM; }
+    if (e == cudaErrorInvalidValue) { cudaGetLastError(); return LR_ERR_SENTINEL; }   // bad offset table
+    return e == cudaSuccess ? LR_OK : cuda_fail(ctx, e);
+}
+
+}  // namespace
+
 lr_status lr_build_arrays(lr_ctx* ctx, lr_stream_t stream, const uint8_t* d_text, int32_t n, int32_t* d_sa,
                           int32_t* d_rank, int32_t* d_lcp, int32_t* rounds) {
     if (!ctx || !d_text || !d_sa || !d_rank || !d_lcp) return LR_ERR_ARG;
     if (check_n(n) != LR_OK) return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr_status st = index_work_for(ctx, n);
+    if (st != LR_OK) return st;
+    if (!ctx->d_off2 && cudaMalloc((void**)&ctx->d_off2, 16) != cudaSuccess) { cudaGetLastError(); return LR_ERR_NOMEM; }
+    cudaStream_t strm = (cudaStream_t)stream;
+    const int64_t h_off[2] = {0, (int64_t)n};
+    cudaError_t e = cudaMemcpyAsync(ctx->d_off2, h_off, sizeof(h_off), cudaMemcpyHostToDevice, strm);
     int r = 0;
-    cudaError_t e = lr::build_arrays(d_text, n, d_sa, d_rank, d_lcp, (cudaStream_t)stream, &r);
-    if (e == cudaErrorMemoryAllocation) return LR_ERR_NOMEM;
-    if (e != cudaSuccess) return cuda_fail(ctx, e);
-    if (rounds) *rounds = r;
-    return LR_OK;
+    if (e == cudaSuccess)
+        e = lr::build_arrays_batch(d_text, n, ctx->d_off2, 1, d_sa, d_rank, d_lcp, ctx->index_work, true, strm, &r);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+    st = index_status(ctx, e);
+    if (st == LR_OK && rounds) *rounds = r;
+    return st;
+}
+
+lr_status lr_batch_build_arrays(lr_ctx* ctx, lr_stream_t stream, const lr_text_batch* batch, int32_t* d_sa,
+                                int32_t* d_rank, int32_t* d_lcp, int32_t* rounds) {
+    if (!ctx || !batch || !batch->d_off || !d_sa || !d_rank || !d_lcp) return LR_ERR_ARG;
+    if (batch->num < 1 || batch->total < 0 || batch->total > kMaxN || (batch->total > 0 && !batch->d_text))
+        return LR_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
+    lr_status st = index_work_for(ctx, batch->total);
+    if (st != LR_OK) return st;
+    cudaStream_t strm = (cudaStream_t)stream;
+    int r = 0;
+    cudaError_t e = lr::build_arrays_batch(batch->d_text, batch->total, batch->d_off, batch->num, d_sa, d_rank,
+                                           d_lcp, ctx->index_work, true, strm, &r);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+    st = index_status(ctx, e);
+    if (st == LR_OK && rounds) *rounds = r;
+    return st;
 }
 
 lr_status lr_query_all_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,

@@ -1,20 +1,25 @@
 // Suffix array, rank and lcp arrays on the device: the step before the
 // longest-repeat query.  The paper builds them on the host and notes that
 // they can be built in parallel on a GPU by prefix doubling (Sec. 4, citing
-// Osipov 2012 and Deo and Keely 2013); this is a prefix-doubling build.
+// Osipov 2012 and Deo and Keely 2013); this is a prefix-doubling build, for
+// one string or for many strings packed back to back (string j owns
+// positions [off[j], off[j+1])) in one pass.
 //
-//  * round 0: every suffix gets the key of its first 7 symbols (9 bits each,
-//    symbol + 1, 0 past the end); the keys are sorted with their positions
-//    (radix sort) and each position's rank becomes the sorted index of the
-//    first key equal to its own (a max-scan over group heads);
-//  * round r >= 1, h = 7 * 2^(r-1): key(i) = (rank(i), rank(i + h) + 1 or 0
-//    past the end), sorted again; ranks are equal iff the first 7 * 2^r
-//    symbols are;
-//  * rounds stop when all n ranks differ: the sorted positions are the
-//    suffix array and the last ranks its inverse;
+//  * round 0: every suffix gets a key of its string index (most significant)
+//    and its first c symbols (9 bits each, symbol + 1, 0 past the end of its
+//    string; c = 7 for one string, fewer when the string index needs bits);
+//    the keys are sorted with their positions (radix sort) and each
+//    position's rank becomes the sorted index of the first key equal to its
+//    own (a max-scan over group heads).  Strings occupy consecutive rank
+//    ranges, [off[j], off[j+1]) for string j;
+//  * round r >= 1, h = c * 2^(r-1): key(i) = (rank(i), rank(i + h) + 1, or 0
+//    past the end of i's string), sorted again; ranks are equal iff the
+//    strings and the first c * 2^r symbols are;
+//  * rounds stop when all ranks differ: sorted position g holds the suffix of
+//    local rank g - off[j];
 //  * lcp of each pair of sa neighbours by binary lifting over the ranks of
-//    every round (longest first: equal ranks at round r mean 7 * 2^r equal
-//    symbols, skip them), then at most six symbol comparisons.
+//    every round (longest first: equal ranks at round r mean c * 2^r equal
+//    symbols, skip them), then fewer than c symbol comparisons.
 #include <cuda_runtime.h>
 #include <cub/cub.cuh>
 #include <cstdint>
@@ -24,64 +29,106 @@ namespace lr {
 
 namespace {
 
-constexpr int kSym0 = 7;               // symbols in the round-0 key (7 x 9 bits)
+// The string holding flattened position g: the last j with off[j] <= g.
+__device__ __forceinline__ long long string_of(const int64_t* __restrict__ off, long long num, long long g) {
+    long long lo = 0, hi = num - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
-__global__ void k_keys0(const uint8_t* __restrict__ text, int32_t n, uint64_t* __restrict__ key,
-                        int32_t* __restrict__ val) {
+__global__ void k_keys0(const uint8_t* __restrict__ text, long long total, const int64_t* __restrict__ off,
+                        long long num, int csyms, uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                        int32_t* __restrict__ end) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint64_t k = 0;
-#pragma unroll
-    for (int j = 0; j < kSym0; ++j) {
-        const uint32_t c = (i + j < n) ? (uint32_t)__ldg(text + i + j) + 1u : 0u;
+    if (i >= total) return;
+    const long long j = string_of(off, num, i);
+    const long long e = __ldg(off + j + 1);
+    uint64_t k = (uint64_t)j;
+    for (int t = 0; t < csyms; ++t) {
+        const uint32_t c = (i + t < e) ? (uint32_t)__ldg(text + i + t) + 1u : 0u;
         k = (k << 9) | c;
     }
     key[i] = k;
     val[i] = (int32_t)i;
+    end[i] = (int32_t)e;
 }
 
-__global__ void k_keys(const int32_t* __restrict__ rank, int32_t n, long long h, uint64_t* __restrict__ key,
-                       int32_t* __restrict__ val) {
+__global__ void k_keys(const int32_t* __restrict__ rank, long long total, long long h, const int32_t* __restrict__ end,
+                       uint64_t* __restrict__ key, int32_t* __restrict__ val) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t second = (i + h < n) ? (uint32_t)__ldg(rank + i + h) + 1u : 0u;
+    if (i >= total) return;
+    const uint32_t second = (i + h < __ldg(end + i)) ? (uint32_t)__ldg(rank + i + h) + 1u : 0u;
     key[i] = ((uint64_t)(uint32_t)__ldg(rank + i) << 32) | second;
     val[i] = (int32_t)i;
 }
 
-// head[j] = j where sorted key j starts a group of equal keys, else 0; the
+// head[g] = g where sorted key g starts a group of equal keys, else 0; the
 // number of groups is added to *groups.
-__global__ void k_heads(const uint64_t* __restrict__ key, int32_t n, int32_t* __restrict__ head,
+__global__ void k_heads(const uint64_t* __restrict__ key, long long total, int32_t* __restrict__ head,
                         unsigned long long* __restrict__ groups) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool h = false;
-    if (j < n) {
-        h = (j == 0) || (key[j] != key[j - 1]);
-        head[j] = h ? (int32_t)j : 0;
+    if (g < total) {
+        h = (g == 0) || (key[g] != key[g - 1]);
+        head[g] = h ? (int32_t)g : 0;
     }
     const unsigned b = __ballot_sync(0xffffffffu, h);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(groups, (unsigned long long)__popc(b));
 }
 
-__global__ void k_scatter_rank(const int32_t* __restrict__ sa, const int32_t* __restrict__ hp, int32_t n,
+__global__ void k_scatter_rank(const int32_t* __restrict__ sorted, const int32_t* __restrict__ hp, long long total,
                                int32_t* __restrict__ rank) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) rank[sa[j]] = hp[j];
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < total) rank[sorted[g]] = hp[g];
 }
 
-__global__ void k_lcp(const uint8_t* __restrict__ text, int32_t n, const int32_t* __restrict__ sa,
-                      const int32_t* __restrict__ levels, int rounds, int32_t* __restrict__ lcp) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > n) return;
-    if (j == 0 || j == n) { lcp[j] = 0; return; }
-    long long x = sa[j - 1], y = sa[j], l = 0;
-    for (int r = rounds - 1; r >= 0; --r) {
-        const long long len = (long long)kSym0 << r;
-        const int32_t* R = levels + (size_t)r * (size_t)n;
-        if (x < n && y < n && __ldg(R + x) == __ldg(R + y)) { l += len; x += len; y += len; }
+// lcp of sorted neighbours g - 1, g of one string, written in the layout the
+// queries take (string j's n_j + 1 entries at off[j] + j), and the string-
+// local sa and rank.
+__global__ void k_lcp(const uint8_t* __restrict__ text, long long total, const int64_t* __restrict__ off,
+                      long long num, const int32_t* __restrict__ sorted, const int32_t* __restrict__ levels,
+                      int rounds, int csyms, const int32_t* __restrict__ end, const int32_t* __restrict__ frank,
+                      int32_t* __restrict__ sa, int32_t* __restrict__ rank, int32_t* __restrict__ lcp) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const long long j = string_of(off, num, g);
+    const long long a = __ldg(off + j);
+    sa[g] = (int32_t)(sorted[g] - a);
+    rank[g] = (int32_t)(frank[g] - a);
+    int32_t out = 0;
+    if (g > a) {
+        long long x = sorted[g - 1], y = sorted[g], l = 0;
+        const long long e = __ldg(end + y);
+        for (int r = rounds - 1; r >= 0; --r) {
+            const long long len = (long long)csyms << r;
+            const int32_t* R = levels + (size_t)r * (size_t)total;
+            if (x < e && y < e && __ldg(R + x) == __ldg(R + y)) { l += len; x += len; y += len; }
+        }
+        for (int t = 0; t < csyms && x < e && y < e && __ldg(text + x) == __ldg(text + y); ++t) { ++l; ++x; ++y; }
+        out = (int32_t)l;
     }
-    for (int t = 0; t < kSym0 && x < n && y < n && __ldg(text + x) == __ldg(text + y); ++t) { ++l; ++x; ++y; }
-    lcp[j] = (int32_t)l;
+    lcp[g + j] = out;                                  // lcp[0] of string j is 0 (g == a)
+}
+
+// The closing sentinel lcp[n_j] = 0 of every string (and the only entry of
+// an empty one).
+__global__ void k_lcp_tails(const int64_t* __restrict__ off, long long num, int32_t* __restrict__ lcp) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < num) lcp[__ldg(off + j + 1) + j] = 0;
+}
+
+// Sets *bad unless off[0] = 0, off[num] = total and off never decreases.
+__global__ void k_check_off(const int64_t* __restrict__ off, long long num, long long total,
+                            unsigned long long* __restrict__ bad) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > num) return;
+    const long long v = __ldg(off + j);
+    bool b = v < 0 || v > total || (j == 0 && v != 0) || (j == num && v != total);
+    if (j < num && __ldg(off + j + 1) < v) b = true;
+    if (b) atomicOr(bad, 1ull);
 }
 
 struct MaxOp {
@@ -90,100 +137,152 @@ struct MaxOp {
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-}  // namespace
-
-// Builds sa, rank and lcp (n + 1 entries) of text[0..n) on `stream`; all
-// device memory it needs is allocated here and freed before returning.
-// Returns cudaErrorMemoryAllocation when it does not fit.
-cudaError_t build_arrays(const uint8_t* text, int32_t n, int32_t* sa, int32_t* rank, int32_t* lcp,
-                         cudaStream_t stream, int* rounds_out) {
-    const size_t nn = (size_t)n;
-    int bits = 1;
-    while (bits < 31 && (1ll << bits) <= (long long)n) ++bits;
-    const int max_rounds = 34;
-    uint64_t *k0 = nullptr, *k1 = nullptr;
-    int32_t *v0 = nullptr, *v1 = nullptr, *head = nullptr, *hp = nullptr, *levels = nullptr;
-    unsigned long long* groups = nullptr;
-    void* tmp = nullptr;
-    size_t tmp_sort = 0, tmp_scan = 0;
-    cudaError_t e = cudaSuccess;
-    auto fail = [&](cudaError_t err) {
-        cudaFree(k0); cudaFree(k1); cudaFree(v0); cudaFree(v1); cudaFree(head); cudaFree(hp);
-        cudaFree(levels); cudaFree(groups); cudaFree(tmp);
-        return err;
-    };
+size_t sort_temp_bytes(long long n) {
+    size_t a = 0, b = 0;
     cub::DoubleBuffer<uint64_t> keys(nullptr, nullptr);
     cub::DoubleBuffer<int32_t> vals(nullptr, nullptr);
-    e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_sort, keys, vals, n, 0, 64, stream);
-    if (e == cudaSuccess) e = cub::DeviceScan::InclusiveScan(nullptr, tmp_scan, head, hp, MaxOp{}, n, stream);
+    cub::DeviceRadixSort::SortPairs(nullptr, a, keys, vals, (int)n, 0, 64, (cudaStream_t)0);
+    cub::DeviceScan::InclusiveScan(nullptr, b, (int32_t*)nullptr, (int32_t*)nullptr, MaxOp{}, (int)n, (cudaStream_t)0);
+    return (a > b ? a : b) + 256;
+}
+
+inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// Layout of the work memory for n positions and `rounds` rank levels.
+size_t index_work_bytes(long long n, int rounds) {
+    const size_t nn = (size_t)n;
+    return al(nn * 8) * 2 + al(nn * 4) * 5 + al((size_t)rounds * nn * 4) + al(64) + al(sort_temp_bytes(n));
+}
+
+cudaError_t IndexWork::alloc(long long n, int rounds) {
+    release();
+    const size_t nn = (size_t)n;
+    bytes = index_work_bytes(n, rounds);
+    cudaError_t e = cudaMalloc((void**)&base, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); base = nullptr; bytes = 0; return cudaErrorMemoryAllocation; }
+    unsigned char* p = base;
+    k0 = (uint64_t*)p; p += al(nn * 8);
+    k1 = (uint64_t*)p; p += al(nn * 8);
+    v0 = (int32_t*)p; p += al(nn * 4);
+    v1 = (int32_t*)p; p += al(nn * 4);
+    head = (int32_t*)p; p += al(nn * 4);
+    hp = (int32_t*)p; p += al(nn * 4);
+    end = (int32_t*)p; p += al(nn * 4);
+    levels = (int32_t*)p; p += al((size_t)rounds * nn * 4);
+    misc = (unsigned long long*)p; p += al(64);
+    tmp = p;
+    tmp_bytes = sort_temp_bytes(n);
+    cap_n = n;
+    cap_rounds = rounds;
+    return cudaSuccess;
+}
+
+void IndexWork::release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    bytes = 0;
+    cap_n = 0;
+    cap_rounds = 0;
+}
+
+// Builds sa, rank (string-local, at the strings' offsets) and lcp (n_j + 1
+// entries per string at off[j] + j) of text[0..total) split by the device
+// offset table off[0..num]; `w` must hold `total` positions.  When more
+// rounds are needed than w holds and `grow` is set, w is reallocated (which
+// waits for the device); otherwise cudaErrorMemoryAllocation.
+cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64_t* off, long long num, int32_t* sa,
+                               int32_t* rank, int32_t* lcp, IndexWork& w, bool grow, cudaStream_t stream,
+                               int* rounds_out) {
+    if (total > w.cap_n) return cudaErrorMemoryAllocation;
+    // every kernel below trusts the offset table: check it first
+    cudaError_t e = cudaMemsetAsync(w.misc, 0, 16, stream);
     if (e != cudaSuccess) return e;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&k0, nn * 8);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&k1, nn * 8);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v0, nn * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v1, nn * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&head, nn * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&hp, nn * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&groups, 8);
-    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_sort > tmp_scan ? tmp_sort : tmp_scan);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(cudaErrorMemoryAllocation); }
-    // ranks of every round, for the lcp lifting; grown a round at a time
-    int cap_rounds = 8;
-    e = cudaMalloc((void**)&levels, (size_t)cap_rounds * nn * 4);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(cudaErrorMemoryAllocation); }
-    keys = cub::DoubleBuffer<uint64_t>(k0, k1);
-    vals = cub::DoubleBuffer<int32_t>(v0, v1);
-    const size_t tmp_bytes = tmp_sort > tmp_scan ? tmp_sort : tmp_scan;
+    k_check_off<<<blocks(num + 1, 256), 256, 0, stream>>>(off, num, total, w.misc + 1);
+    e = cudaMemcpyAsync(&w.groups_host, w.misc + 1, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    if (w.groups_host != 0) return cudaErrorInvalidValue;
+    k_lcp_tails<<<blocks(num, 256), 256, 0, stream>>>(off, num, lcp);
+    if (total == 0) {
+        if (rounds_out) *rounds_out = 0;
+        return cudaGetLastError();
+    }
+    const size_t nn = (size_t)total;
+    int jobbits = 0;
+    while (jobbits < 40 && (1ll << jobbits) < num) ++jobbits;
+    const int csyms = (63 - jobbits) / 9;
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) <= total) ++bits;
+    cub::DoubleBuffer<uint64_t> keys(w.k0, w.k1);
+    cub::DoubleBuffer<int32_t> vals(w.v0, w.v1);
     int r = 0;
     for (;; ++r) {
-        if (r >= max_rounds) return fail(cudaErrorUnknown);
-        if (r >= cap_rounds) {                           // more rounds than room: double the level store
-            int32_t* bigger = nullptr;
-            if (cudaMalloc((void**)&bigger, (size_t)cap_rounds * 2 * nn * 4) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(cudaErrorMemoryAllocation);
-            }
-            e = cudaMemcpyAsync(bigger, levels, (size_t)cap_rounds * nn * 4, cudaMemcpyDeviceToDevice, stream);
+        if (r >= 40) return cudaErrorUnknown;
+        if (r >= w.cap_rounds) {                          // more rounds than the level store holds
+            if (!grow) return cudaErrorMemoryAllocation;
+            IndexWork bigger;
+            e = bigger.alloc(w.cap_n, w.cap_rounds * 2);
+            if (e != cudaSuccess) return e;
+            e = cudaMemcpyAsync(bigger.levels, w.levels, (size_t)w.cap_rounds * nn * 4, cudaMemcpyDeviceToDevice,
+                                stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.end, w.end, nn * 4, cudaMemcpyDeviceToDevice, stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            cudaFree(levels);
-            levels = bigger;
-            cap_rounds *= 2;
-            if (e != cudaSuccess) return fail(e);
+            if (e != cudaSuccess) { bigger.release(); return e; }
+            w.release();
+            w = bigger;
+            bigger.base = nullptr;                        // owned by w now
+            keys = cub::DoubleBuffer<uint64_t>(w.k0, w.k1);
+            vals = cub::DoubleBuffer<int32_t>(w.v0, w.v1);
         }
         int end_bit;
         if (r == 0) {
-            k_keys0<<<blocks(n, 256), 256, 0, stream>>>(text, n, keys.Current(), vals.Current());
-            end_bit = 9 * kSym0;
+            k_keys0<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, csyms, keys.Current(),
+                                                            vals.Current(), w.end);
+            end_bit = jobbits + 9 * csyms;
         } else {
-            const long long h = (long long)kSym0 << (r - 1);
-            k_keys<<<blocks(n, 256), 256, 0, stream>>>(levels + (size_t)(r - 1) * nn, n, h, keys.Current(),
-                                                       vals.Current());
+            const long long h = (long long)csyms << (r - 1);
+            k_keys<<<blocks(total, 256), 256, 0, stream>>>(w.levels + (size_t)(r - 1) * nn, total, h, w.end,
+                                                           keys.Current(), vals.Current());
             end_bit = 32 + bits;
         }
-        size_t tb = tmp_bytes;
-        e = cub::DeviceRadixSort::SortPairs(tmp, tb, keys, vals, n, 0, end_bit, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(groups, 0, 8, stream);
-        if (e != cudaSuccess) return fail(e);
-        k_heads<<<blocks(n, 256), 256, 0, stream>>>(keys.Current(), n, head, groups);
-        tb = tmp_bytes;
-        e = cub::DeviceScan::InclusiveScan(tmp, tb, head, hp, MaxOp{}, n, stream);
-        if (e != cudaSuccess) return fail(e);
-        k_scatter_rank<<<blocks(n, 256), 256, 0, stream>>>(vals.Current(), hp, n, levels + (size_t)r * nn);
-        unsigned long long g = 0;
-        e = cudaMemcpyAsync(&g, groups, 8, cudaMemcpyDeviceToHost, stream);
+        size_t tb = w.tmp_bytes;
+        e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, end_bit, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 8, stream);
+        if (e != cudaSuccess) return e;
+        k_heads<<<blocks(total, 256), 256, 0, stream>>>(keys.Current(), total, w.head, w.misc);
+        tb = w.tmp_bytes;
+        e = cub::DeviceScan::InclusiveScan(w.tmp, tb, w.head, w.hp, MaxOp{}, (int)total, stream);
+        if (e != cudaSuccess) return e;
+        k_scatter_rank<<<blocks(total, 256), 256, 0, stream>>>(vals.Current(), w.hp, total, w.levels + (size_t)r * nn);
+        e = cudaMemcpyAsync(&w.groups_host, w.misc, 8, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return fail(e);
-        if (g == (unsigned long long)n) break;
+        if (e != cudaSuccess) return e;
+        if (w.groups_host == (unsigned long long)total) break;
     }
     const int rounds = r + 1;
-    e = cudaMemcpyAsync(sa, vals.Current(), nn * 4, cudaMemcpyDeviceToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(rank, levels + (size_t)r * nn, nn * 4, cudaMemcpyDeviceToDevice, stream);
-    if (e != cudaSuccess) return fail(e);
-    k_lcp<<<blocks((long long)n + 1, 256), 256, 0, stream>>>(text, n, vals.Current(), levels, rounds, lcp);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    k_lcp<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, vals.Current(), w.levels, rounds, csyms,
+                                                  w.end, w.levels + (size_t)r * nn, sa, rank, lcp);
     if (rounds_out) *rounds_out = rounds;
-    return fail(e);
+    return cudaGetLastError();
+}
+
+// One string: the work memory is allocated here and freed before returning.
+cudaError_t build_arrays(const uint8_t* text, int32_t n, int32_t* sa, int32_t* rank, int32_t* lcp,
+                         cudaStream_t stream, int* rounds_out) {
+    IndexWork w;
+    cudaError_t e = w.alloc(n, 8);
+    if (e != cudaSuccess) return e;
+    int64_t* off = nullptr;                                         // {0, n}
+    if (cudaMalloc((void**)&off, 16) != cudaSuccess) { cudaGetLastError(); w.release(); return cudaErrorMemoryAllocation; }
+    const int64_t h_off[2] = {0, (int64_t)n};
+    e = cudaMemcpyAsync(off, h_off, sizeof(h_off), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = build_arrays_batch(text, n, off, 1, sa, rank, lcp, w, true, stream, rounds_out);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFree(off);
+    w.release();
+    return e;
 }
 
 }  // namespace lr

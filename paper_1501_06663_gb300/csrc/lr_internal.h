@@ -110,8 +110,31 @@ cudaError_t launch_raw_query(const int32_t* rank, const int32_t* lcp, int32_t n,
 cudaError_t launch_walk_stats(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s, int32_t* alpha,
                               int32_t* beta, unsigned long long* stats, cudaStream_t stream);
 
-// Suffix array, rank and lcp of a device text by prefix doubling
-// (lr_index.cu); allocates and frees its own work memory.
+// Suffix array, rank and lcp of device texts by prefix doubling
+// (lr_index.cu).  IndexWork is the work memory for up to cap_n positions
+// and cap_rounds doubling rounds (released explicitly).
+struct IndexWork {
+    unsigned char* base = nullptr;
+    size_t bytes = 0;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    int32_t *v0 = nullptr, *v1 = nullptr, *head = nullptr, *hp = nullptr, *end = nullptr, *levels = nullptr;
+    unsigned long long* misc = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    long long cap_n = 0;
+    int cap_rounds = 0;
+    unsigned long long groups_host = 0;
+    cudaError_t alloc(long long n, int rounds);
+    void release();
+};
+size_t index_work_bytes(long long n, int rounds);
+// Many strings (string j = text[off[j], off[j+1]), off on the device): sa and
+// rank string-local at the strings' offsets, lcp (n_j + 1 entries) at
+// off[j] + j.  Waits for `stream` once per round.
+cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64_t* off, long long num, int32_t* sa,
+                               int32_t* rank, int32_t* lcp, IndexWork& w, bool grow, cudaStream_t stream,
+                               int* rounds_out);
+// One string; allocates and frees its own work memory.
 cudaError_t build_arrays(const uint8_t* text, int32_t n, int32_t* sa, int32_t* rank, int32_t* lcp,
                          cudaStream_t stream, int* rounds_out);
 
