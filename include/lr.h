@@ -308,18 +308,23 @@ typedef struct {
     double hbm_fraction;           /* share of the free device memory the slots may take; 0 = 0.5 */
     double starts_factor;          /* initial starts buffer of a slot, in entries per position; 0 = 2
                                       (it grows, within the budget, when a batch needs more) */
+    int32_t text_jobs;             /* nonzero: slots also take text jobs (sa / rank / lcp built on
+                                      the GPU; about 90 more bytes of device memory per position) */
 } lr_server_config;
 
 typedef struct {
     const int32_t* h_sa;           /* host, n entries, or NULL */
     const int32_t* h_rank;         /* host, n entries, or NULL (sa wins when both are given) */
-    const int32_t* h_lcp;          /* host, n + 1 entries */
+    const int32_t* h_lcp;          /* host, n + 1 entries; NULL for a text job */
     int32_t n;                     /* 1 <= n <= max_batch_positions */
     int32_t* h_lr_len;             /* host outputs, as lr_query_all: n */
     int32_t* h_lr_start;           /* n, string-local positions */
     int64_t* h_offsets;            /* n + 1 */
     int32_t* h_starts;             /* starts_capacity entries (NULL when 0) */
     int64_t starts_capacity;
+    const uint8_t* h_text;         /* text job: the string itself (n bytes) and no sa, rank or lcp; its
+                                      arrays are built on the GPU with the rest of its batch
+                                      (lr_batch_build_arrays); needs a server started with text_jobs */
 } lr_job;
 
 enum { LR_JOB_QUEUED = 0, LR_JOB_ADMITTED = 1, LR_JOB_RUNNING = 2, LR_JOB_DONE = 3, LR_JOB_CANCELLED = 4 };

@@ -55,14 +55,15 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("max_batch_positions", ctypes.c_int64), ("max_batch_jobs", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("batch_window_us", ctypes.c_int32), ("hbm_fraction", ctypes.c_double),
-                ("starts_factor", ctypes.c_double)]
+                ("starts_factor", ctypes.c_double), ("text_jobs", ctypes.c_int32)]
 
 
 class Job(ctypes.Structure):
     """lr_job: one query job with host buffers."""
     _fields_ = [("h_sa", ctypes.c_void_p), ("h_rank", ctypes.c_void_p), ("h_lcp", ctypes.c_void_p),
                 ("n", ctypes.c_int32), ("h_lr_len", ctypes.c_void_p), ("h_lr_start", ctypes.c_void_p),
-                ("h_offsets", ctypes.c_void_p), ("h_starts", ctypes.c_void_p), ("starts_capacity", ctypes.c_int64)]
+                ("h_offsets", ctypes.c_void_p), ("h_starts", ctypes.c_void_p), ("starts_capacity", ctypes.c_int64),
+                ("h_text", ctypes.c_void_p)]
 
 
 class ServerStats(ctypes.Structure):
@@ -556,14 +557,17 @@ class Server:
         self.handle = lr_server_start(c)
         self._jobs = {}
 
-    def submit(self, lcp, sa=None, rank=None, capacity: int | None = None, pinned: bool = False, out=None):
+    def submit(self, lcp=None, sa=None, rank=None, capacity: int | None = None, pinned: bool = False, out=None,
+               text=None):
         """Queues one job; returns its id (raises LRError on LR_ERR_BUSY / NOMEM / ARG).
 
-        `out` = (lr_len, lr_start, offsets, starts) host arrays to fill
-        instead of newly allocated ones (capacity = len(starts)).
+        Give lcp with sa or rank, or `text` alone (uint8; its arrays are built
+        on the GPU; the server must be started with text_jobs=1).  `out` =
+        (lr_len, lr_start, offsets, starts) host arrays to fill instead of
+        newly allocated ones (capacity = len(starts)).
         """
         import numpy as np
-        n = int(len(sa) if sa is not None else len(rank))
+        n = int(len(text) if text is not None else (len(sa) if sa is not None else len(rank)))
         if out is not None:
             outs = tuple(out)
             cap = int(len(outs[3]))
@@ -579,10 +583,10 @@ class Server:
                 outs = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n + 1, np.int64),
                         np.empty(max(cap, 1), np.int32))
         job = Job(_ptr(sa), _ptr(rank), _ptr(lcp), n, _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), _ptr(outs[3]),
-                  cap)
+                  cap, _ptr(text))
         st, jid = lr_server_submit(self.handle, job)
         _check(st, "lr_server_submit")
-        self._jobs[jid] = (sa, rank, lcp, outs)
+        self._jobs[jid] = (sa if text is None else text, rank, lcp, outs)
         return jid
 
     def wait(self, job_id: int, timeout_ms: int = -1):

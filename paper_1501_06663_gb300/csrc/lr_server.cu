@@ -25,6 +25,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr size_t kAlignS = 256;
+constexpr int kTextRounds = 12;                      // doubling rounds a text slot holds (grown on demand)
 inline size_t align_s(size_t v) { return (v + kAlignS - 1) / kAlignS * kAlignS; }
 
 // Turns the flattened results of a batched query into per-job ones: every
@@ -57,10 +58,12 @@ __global__ void k_localize(int32_t total, int32_t num, const int64_t* __restrict
     }
 }
 
+enum JobKind { kSaJob, kRankJob, kTextJob };
+
 struct Job {
     int64_t id = 0;
     lr_job spec{};
-    bool use_sa = true;
+    JobKind kind = kSaJob;
     int32_t state = LR_JOB_QUEUED;
     lr_status result = LR_OK;
     int64_t total = 0;
@@ -90,7 +93,9 @@ struct Slot {
     unsigned* h_err = nullptr;
     std::vector<Job*> jobs;
     int64_t used = 0;
-    bool use_sa = true;
+    JobKind kind = kSaJob;
+    uint8_t* d_text = nullptr;                       // text jobs: the strings, and the build's work memory
+    lr::IndexWork index_work;
     Clock::time_point t_first;
 };
 
@@ -134,10 +139,10 @@ void CUDART_CB on_stream_done(void* p) {
 
 // Device bytes of one slot (without d_starts) for P positions and J jobs.
 struct SlotLayout {
-    size_t in, lcp, off, len, start, offsets, locoff, jobtot, err, scratch, total;
+    size_t in, lcp, off, len, start, offsets, locoff, jobtot, err, scratch, text, total;
 };
 
-SlotLayout slot_layout(int64_t P, int32_t J) {
+SlotLayout slot_layout(int64_t P, int32_t J, bool text) {
     SlotLayout L;
     size_t o = 0;
     L.in = o;       o = align_s(o + (size_t)P * 4);
@@ -150,6 +155,7 @@ SlotLayout slot_layout(int64_t P, int32_t J) {
     L.jobtot = o;   o = align_s(o + (size_t)J * 8);
     L.err = o;      o = align_s(o + 256);
     L.scratch = o;  o = align_s(o + lr::scratch_size(P));
+    L.text = o;     o = align_s(o + (text ? (size_t)P : 0));
     L.total = o;
     return L;
 }
@@ -159,6 +165,7 @@ void free_slot(Slot& s) {
     if (s.mem) cudaFree(s.mem);
     if (s.d_starts) cudaFree(s.d_starts);
     if (s.h_off) cudaFreeHost(s.h_off);
+    s.index_work.release();
     if (s.stream) cudaStreamDestroy(s.stream);
     s.mem = nullptr; s.d_starts = nullptr; s.h_off = nullptr; s.stream = nullptr;
 }
@@ -182,6 +189,12 @@ cudaError_t alloc_slot(lr_server* S, Slot& s, const SlotLayout& L, int64_t cap) 
     s.d_jobtot = (int64_t*)(b + L.jobtot);
     s.d_err = (unsigned*)(b + L.err);
     s.scratch = b + L.scratch;
+    s.d_text = S->cfg.text_jobs ? b + L.text : nullptr;
+    if (S->cfg.text_jobs) {
+        e = s.index_work.alloc(S->P, kTextRounds);
+        if (e != cudaSuccess) return e;
+        S->device_bytes += (int64_t)s.index_work.bytes;
+    }
     s.h_jobtot = s.h_off + (S->J + 1);
     s.h_err = (unsigned*)(s.h_jobtot + S->J);
     S->device_bytes += (int64_t)L.total + cap * 4;
@@ -212,9 +225,20 @@ cudaError_t launch_batch(lr_server* S, Slot& s) {
     cudaError_t e = cudaMemcpyAsync(s.d_off, s.h_off, (size_t)(num + 1) * 8, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.d_err, 0, 4, s.stream);
     if (e != cudaSuccess) return e;
+    if (s.kind == kTextJob) {
+        // sa (into d_in), rank (into d_len, overwritten by the query) and
+        // lcp of every string of the batch, built on the GPU; this waits for
+        // the slot's stream once per doubling round
+        const int64_t before = (int64_t)s.index_work.bytes;
+        e = lr::build_arrays_batch(s.d_text, total, s.d_off, num, s.d_in, s.d_len, s.d_lcp, s.index_work, true,
+                                   s.stream, nullptr);
+        S->device_bytes += (int64_t)s.index_work.bytes - before;
+        if (e != cudaSuccess) return e;
+    }
+    const bool use_sa = s.kind != kRankJob;
     lr::Scratch sc;
     lr::carve_scratch(s.scratch, S->P, total, s.d_err, &sc);
-    e = lr::launch_query(s.use_sa ? s.d_in : nullptr, s.use_sa ? nullptr : s.d_in, s.d_lcp, total, sc, s.d_len,
+    e = lr::launch_query(use_sa ? s.d_in : nullptr, use_sa ? nullptr : s.d_in, s.d_lcp, total, sc, s.d_len,
                          s.d_start, s.d_offsets, s.d_starts, s.cap, true, s.stream, nullptr, nullptr,
                          lr::Segs{s.d_off, num}, lr::Shape{});
     if (e != cudaSuccess) return e;
@@ -256,7 +280,8 @@ void run_solo(lr_server* S, Slot& s) {
             lr::carve_scratch(s.scratch, S->P, n, s.d_err, &sc);
             cudaError_t e = cudaMemsetAsync(s.d_err, 0, 4, s.stream);
             if (e == cudaSuccess)
-                e = lr::launch_query(s.use_sa ? s.d_in + job->off : nullptr, s.use_sa ? nullptr : s.d_in + job->off,
+                e = lr::launch_query(s.kind != kRankJob ? s.d_in + job->off : nullptr,
+                                     s.kind != kRankJob ? nullptr : s.d_in + job->off,
                                      s.d_lcp + job->off + j, n, sc, s.d_len + job->off, s.d_start + job->off, d_loc,
                                      s.d_starts, s.cap, true, s.stream, nullptr, nullptr);
             if (e == cudaSuccess)
@@ -369,11 +394,11 @@ int admit_locked(lr_server* S, std::vector<Job*>& admitted) {
             f.used = 0;
             f.blocked = false;
             f.copy_failed = false;
-            f.use_sa = job->use_sa;
+            f.kind = job->kind;
             f.jobs.clear();
         }
         Slot& f = S->slots[S->filling];
-        if (f.used + job->spec.n > S->P || (int)f.jobs.size() >= S->J || f.use_sa != job->use_sa) {
+        if (f.used + job->spec.n > S->P || (int)f.jobs.size() >= S->J || f.kind != job->kind) {
             f.blocked = true;
             break;
         }
@@ -396,11 +421,15 @@ cudaError_t copy_in(Slot& s, const std::vector<Job*>& admitted) {
     for (Job* job : admitted) {
         const int j = job->idx;
         const lr_job& q = job->spec;
-        const int32_t* src = job->use_sa ? q.h_sa : q.h_rank;
-        e = cudaMemcpyAsync(s.d_in + job->off, src, (size_t)q.n * 4, cudaMemcpyHostToDevice, s.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s.d_lcp + job->off + j, q.h_lcp, (size_t)(q.n + 1) * 4, cudaMemcpyHostToDevice,
-                                s.stream);
+        if (job->kind == kTextJob) {
+            e = cudaMemcpyAsync(s.d_text + job->off, q.h_text, (size_t)q.n, cudaMemcpyHostToDevice, s.stream);
+        } else {
+            const int32_t* src = job->kind == kSaJob ? q.h_sa : q.h_rank;
+            e = cudaMemcpyAsync(s.d_in + job->off, src, (size_t)q.n * 4, cudaMemcpyHostToDevice, s.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s.d_lcp + job->off + j, q.h_lcp, (size_t)(q.n + 1) * 4, cudaMemcpyHostToDevice,
+                                    s.stream);
+        }
         if (e != cudaSuccess) break;
     }
     return e;
@@ -522,9 +551,9 @@ lr_status lr_server_start(const lr_server_config* cfg_in, lr_server** out) {
     S->P = cfg.max_batch_positions;
     S->J = cfg.max_batch_jobs;
     S->budget = (size_t)((double)free_b * cfg.hbm_fraction);
-    const SlotLayout L = slot_layout(S->P, S->J);
+    const SlotLayout L = slot_layout(S->P, S->J, cfg.text_jobs != 0);
     const int64_t cap0 = (int64_t)(cfg.starts_factor * (double)S->P) + 1024;
-    const size_t per_slot = L.total + (size_t)cap0 * 4;
+    const size_t per_slot = L.total + (size_t)cap0 * 4 + (cfg.text_jobs ? lr::index_work_bytes(S->P, kTextRounds) : 0);
     const int fit = (int)std::min<size_t>((size_t)cfg.slots, S->budget / per_slot);
     if (fit < 1) { delete S; return LR_ERR_NOMEM; }
     S->nslots = fit;
@@ -550,14 +579,16 @@ lr_status lr_server_start(const lr_server_config* cfg_in, lr_server** out) {
 
 lr_status lr_server_submit(lr_server* S, const lr_job* q, int64_t* job_id) {
     if (!S || !q || !job_id) return LR_ERR_ARG;
-    if (q->n < 1 || !q->h_lcp || (!q->h_sa && !q->h_rank) || !q->h_lr_len || !q->h_lr_start || !q->h_offsets)
-        return LR_ERR_ARG;
+    const bool text = q->h_text != nullptr && !q->h_sa && !q->h_rank && !q->h_lcp;
+    if (q->n < 1 || !q->h_lr_len || !q->h_lr_start || !q->h_offsets) return LR_ERR_ARG;
+    if (!text && (!q->h_lcp || (!q->h_sa && !q->h_rank))) return LR_ERR_ARG;
+    if (text && !S->cfg.text_jobs) return LR_ERR_ARG;
     if (q->starts_capacity < 0 || (q->starts_capacity > 0 && !q->h_starts)) return LR_ERR_ARG;
     if (q->n > S->P) return LR_ERR_NOMEM;
     Job* job = new (std::nothrow) Job();
     if (!job) return LR_ERR_NOMEM;
     job->spec = *q;
-    job->use_sa = q->h_sa != nullptr;
+    job->kind = text ? kTextJob : (q->h_sa ? kSaJob : kRankJob);
     job->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stopping || S->queued >= S->cfg.max_queue) { delete job; return LR_ERR_BUSY; }

@@ -178,3 +178,38 @@ def test_admission_limits_cancel_and_stop(lrmod):
                 pass
     finally:
         srv.close()
+
+
+def test_text_jobs_build_their_arrays_on_the_gpu(lrmod, ctx):
+    """Jobs that give only their string: the server builds sa / rank / lcp on
+    the GPU with the rest of the batch; results equal the oracle's on the
+    host-prepped arrays and the query alone; text and array jobs mix."""
+    text, off, _ = W.serving_mix(30, seed=41, median=20000, floor_len=64, cap=200000)
+    strings = [text[int(off[j]):int(off[j + 1])].copy() for j in range(30)]
+    srv = lrmod.Server(0, max_batch_positions=1 << 21, batch_window_us=3000, text_jobs=1)
+    try:
+        ids = []
+        for k, s in enumerate(strings):
+            if k % 5 == 4:                                   # every fifth job brings host-prepped arrays
+                sa, rank, lcp = W.prep(s)
+                ids.append(srv.submit(lcp, sa=sa))
+            else:
+                ids.append(srv.submit(text=s))
+        results = [srv.wait(i, timeout_ms=120000) for i in ids]
+        stats = srv.stats()
+    finally:
+        srv.close()
+    for k, (s, res) in enumerate(zip(strings, results)):
+        sa, rank, lcp = W.prep(s)
+        _check_job(res, rank, lcp, "text job %d" % k)
+    assert stats["completed"] == len(strings)
+
+
+def test_text_jobs_need_a_text_server(lrmod):
+    srv = lrmod.Server(0, max_batch_positions=1 << 16)
+    try:
+        with pytest.raises(lrmod.LRError) as e:
+            srv.submit(text=np.frombuffer(b"abcabc", np.uint8).copy())
+        assert e.value.status == lrmod.LR_ERR_ARG
+    finally:
+        srv.close()
