@@ -236,15 +236,24 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     // cost in a warp would be the longest window of its 32 lanes).  Other
     // runs take the walk of best_of.
     //
-    // Per run the lane keeps best[] (longest length) and pk[] packed:
+    // Per run the lane keeps pk[], packed (the longest length is stored at
+    // once, and read back from the leftmost holder when needed again):
     //   staged tiles:  bits 0..12 leftmost holder v (0x1fff: none); bit 31
     //                  clear: bits 13..30 = holders as a mask from v (bit 0 =
     //                  v); bit 31 set: bits 13..30 = number of holders;
     //   other tiles:   the number of holders.
     constexpr uint32_t kNone = 0x1fffu;
-    int32_t best[kChunksPerWarp];
     uint32_t pk[kChunksPerWarp];
     unsigned (*RT)[kWarp] = sm.rt[warp];
+    // the longest length and the leftmost holder's start of a position are
+    // stored as soon as its run is done (Algorithm 2's output)
+    auto store_leftmost = [&](int c, int32_t b, int32_t vb) {
+        const int32_t k = k0 + c * kWarp + lane;
+        if (k < n) {
+            __stcs(lr_len + k, b);
+            __stcs(lr_start + k, b > 0 ? start_of(vb) : -1);
+        }
+    };
 #pragma unroll
     for (int q = 0; q < kChunksPerWarp; ++q) {
         const int c = q * kWarps + warp;
@@ -285,12 +294,12 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                 p = hold < (1u << 18) ? (v | (hold << 13)) : (v | ((uint32_t)__popc(hold) << 13) | 0x80000000u);
             }
             __syncwarp();                                         // before the next run rewrites RT
-            best[q] = b;
             pk[q] = p;
+            store_leftmost(c, b, (int32_t)(p & kNone));
         } else {
             int32_t b, vb, ct;
             best_of(lw, hi, b, vb, ct);
-            best[q] = b;
+            store_leftmost(c, b, vb);
             if (!staged) pk[q] = (uint32_t)ct;
             else if (ct == 0) pk[q] = kNone;
             else if (ct == 1) pk[q] = (uint32_t)vb | (1u << 13);
@@ -332,26 +341,6 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             }
         }
     }
-#pragma unroll
-    for (int q = 0; q < kChunksPerWarp; ++q) {
-        const int c = q * kWarps + warp;
-        const int32_t k = k0 + c * kWarp + lane;
-        if (k < n) {
-            __stcs(lr_len + k, best[q]);
-            int32_t st = -1;
-            if (best[q] > 0) {
-                if (staged) {
-                    st = start_of((int32_t)(pk[q] & kNone));
-                } else {                                          // leftmost holder: first of the window
-                    int32_t lw, hi;
-                    window(c, lw, hi);
-                    for (int32_t v = lw; v <= hi; ++v)
-                        if (__ldg(gce + v) - __ldg(gcs + v) + 1 == best[q]) { st = __ldg(gcs + v); break; }
-                }
-            }
-            __stcs(lr_start + k, st);
-        }
-    }
 
     if constexpr (kAll) {
         __syncthreads();
@@ -388,9 +377,16 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             } else {
                 int32_t lw, hi;
                 window(c, lw, hi);
+                int32_t bq;                                       // the longest length, again
+                if (staged) {
+                    bq = SCL[p & kNone];
+                } else {
+                    int32_t vb_, ct_;
+                    best_of(lw, hi, bq, vb_, ct_);
+                }
                 for (int32_t v = staged ? (int32_t)(p & kNone) : lw; v <= hi; ++v) {
                     const int32_t len = staged ? SCL[v] : __ldg(gce + v) - __ldg(gcs + v) + 1;
-                    if (len == best[q]) {
+                    if (len == bq) {
                         if (o < capacity) __stcs(starts + o, start_of(v));
                         ++o;
                     }
