@@ -123,6 +123,12 @@ struct lr_server {
     std::deque<int> ready;
     int running = 0;
     std::thread worker;
+    // text slots are launched by builder threads: their array build waits on
+    // the stream once per doubling round, which would stall the worker
+    std::vector<std::thread> builders;
+    std::deque<int> to_build;
+    std::condition_variable cv_build;
+    bool builders_stop = false;
 
     int64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, batches = 0, positions = 0;
     std::vector<double> lat_us;
@@ -435,6 +441,26 @@ cudaError_t copy_in(Slot& s, const std::vector<Job*>& admitted) {
     return e;
 }
 
+void builder_main(lr_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        S->cv_build.wait(lk, [&]() { return S->builders_stop || !S->to_build.empty(); });
+        if (S->to_build.empty()) return;                 // stopping, nothing left
+        Slot& s = S->slots[S->to_build.front()];
+        S->to_build.pop_front();
+        lk.unlock();
+        cudaError_t e = launch_batch(S, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail_all(s, LR_ERR_CUDA);
+            cudaStreamSynchronize(s.stream);
+            finish(S, s);
+        }
+        lk.lock();
+    }
+}
+
 void worker_main(lr_server* S) {
     cudaSetDevice(S->device);
     std::vector<Job*> admitted;
@@ -482,6 +508,12 @@ void worker_main(lr_server* S) {
             ++S->running;
             ++S->batches;
             for (Job* job : s.jobs) job->state = LR_JOB_RUNNING;
+            if (s.kind == kTextJob && !S->builders.empty()) {
+                S->to_build.push_back((int)(&s - S->slots.get()));
+                S->cv_build.notify_one();
+                did = true;
+                continue;
+            }
             lk.unlock();
             cudaError_t e = launch_batch(S, s);
             if (e != cudaSuccess) {
@@ -567,8 +599,16 @@ lr_status lr_server_start(const lr_server_config* cfg_in, lr_server** out) {
         }
     }
     try {
+        if (cfg.text_jobs)
+            for (int i = 0; i < cfg.max_inflight; ++i) S->builders.emplace_back(builder_main, S);
         S->worker = std::thread(worker_main, S);
     } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->builders_stop = true;
+        }
+        S->cv_build.notify_all();
+        for (auto& t : S->builders) if (t.joinable()) t.join();
         for (int k = 0; k < fit; ++k) free_slot(S->slots[k]);
         delete S;
         return LR_ERR_NOMEM;
@@ -694,6 +734,12 @@ lr_status lr_server_stop(lr_server* S) {
         S->cv_done.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->builders_stop = true;
+    }
+    S->cv_build.notify_all();
+    for (auto& t : S->builders) if (t.joinable()) t.join();
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(S->device);
