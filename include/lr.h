@@ -42,9 +42,10 @@
  *  - Calls are asynchronous on `stream` (NULL = the legacy default stream)
  *    unless they take an h_* output, which makes them wait for the stream.
  *  - The library owns only its scratch (tile status words, the compact LLR
- *    array, the partition buffers: about 16 bytes per position), cached in
- *    the context and grown on demand; a context must not be used from two
- *    host threads at once.
+ *    array, the partition buffers: about 20 bytes per position; the device
+ *    copies of lr_query_all_host; the work memory of the GPU array builds),
+ *    cached in the context and grown on demand; a context must not be used
+ *    from two host threads at once.
  *  - No C++ exception crosses this interface.  Errors are returned as
  *    lr_status.  Malformed device inputs (a rank outside [0, n), lcp[0] or
  *    lcp[n] not 0) are detected by the kernels, never read out of bounds,
@@ -395,7 +396,8 @@ lr_status lr_query_all_static(lr_stream_t stream,
 
 /*
  * Kernels launched by the most recent query of this context (for the
- * benchmark's launch accounting): 4 with sa, 2 with rank only.
+ * benchmark's launch accounting): 4 with sa, 2 with rank only, one more for
+ * a batch; 2 for the raw-LLR variant, 4 for lr_walk_stats.
  */
 int32_t lr_last_launch_count(lr_ctx* ctx);
 
