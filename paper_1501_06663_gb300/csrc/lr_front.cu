@@ -299,14 +299,21 @@ size_t part_smem_bytes(int nb) {
 size_t part2_smem_bytes() { return (size_t)(3 * kSubPerSuper + 1) * 4 + (size_t)kPartRound * 6; }
 
 // Exclusive scan of hist[0..nb) into loff[0..nb] by the whole CTA
-// (kPartThreads threads, nb <= 2 * kPartThreads), and one global atomic per
-// non-empty bucket to reserve the round's room: base[b] = old cursor.
-__device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned* cursor) {
+// (kPartThreads threads, R consecutive buckets each, nb <= R * kPartThreads),
+// and one global atomic per non-empty bucket to reserve the round's room:
+// base[b] = old cursor.
+template <int R>
+__device__ __forceinline__ void part_reserve_r(const PartSmem& p, int nb, unsigned* cursor) {
     __shared__ uint32_t wsum[kPartThreads / kWarp];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t a = (2 * tid < nb) ? p.hist[2 * tid] : 0u;
-    const uint32_t c = (2 * tid + 1 < nb) ? p.hist[2 * tid + 1] : 0u;
-    const int incl = warp_incl_scan((int)(a + c));
+    uint32_t a[R], sum = 0;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * tid + u;
+        a[u] = (b < nb) ? p.hist[b] : 0u;
+        sum += a[u];
+    }
+    const int incl = warp_incl_scan((int)sum);
     if (lane == kWarp - 1) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
@@ -316,15 +323,23 @@ __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned
         if (lane == kWarp - 1) p.loff[nb] = wi;
     }
     __syncthreads();
-    const uint32_t ex = wsum[warp] + incl - a - c;
-    if (2 * tid < nb) {
-        p.loff[2 * tid] = ex;
-        if (a) p.base[2 * tid] = atomicAdd(cursor + (size_t)(2 * tid) * kCursorStride, a);
+    uint32_t ex = wsum[warp] + incl - sum;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * tid + u;
+        if (b < nb) {
+            p.loff[b] = ex;
+            if (a[u]) p.base[b] = atomicAdd(cursor + (size_t)b * kCursorStride, a[u]);
+        }
+        ex += a[u];
     }
-    if (2 * tid + 1 < nb) {
-        p.loff[2 * tid + 1] = ex + a;
-        if (c) p.base[2 * tid + 1] = atomicAdd(cursor + (size_t)(2 * tid + 1) * kCursorStride, c);
-    }
+}
+
+// up to 2048 super-buckets (n <= 2^31 positions in super-buckets of 2^20)
+__device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned* cursor) {
+    static_assert(4 * kPartThreads >= 2048, "partition CTAs too small for 2048 super-buckets");
+    if (nb <= 2 * kPartThreads) part_reserve_r<2>(p, nb, cursor);
+    else part_reserve_r<4>(p, nb, cursor);
 }
 
 // Level 1: Lemma 1 in rank order, then the partition of the packed entries
@@ -336,7 +351,7 @@ __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned
 // the length of the last position of every bucket goes to halo (the next
 // bucket's predecessor).
 template <bool kBatch>
-__global__ void __launch_bounds__(kPartThreads, 2)
+__global__ void __launch_bounds__(kPartThreads, kPartBlocks)
 k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs, int tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long load_bar;
@@ -451,7 +466,7 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
 // Level 2: each CTA takes kPartRound entries of one super-bucket and splits
 // them into its kSubPerSuper buckets, entries <position mod 2^15, field>
 // (field = L, or kEsc17 when L is in lbig), the same way as level 1.
-__global__ void __launch_bounds__(kPartThreads, 2)
+__global__ void __launch_bounds__(kPartThreads, kPartBlocks)
 k_part2(int32_t n, Scratch s) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PartSmem P = part_smem(smem_raw, kSubPerSuper);

@@ -20,9 +20,10 @@ constexpr int kBucketLog = 15;
 constexpr int kBucket = 1 << kBucketLog;       // positions per bucket (one bucket CTA)
 constexpr int kSubPerSuper = kSuper / kBucket; // 32
 constexpr int kBucketThreads = 512;            // threads of the bucket CTA
-constexpr int kPartThreads = 1024;             // threads of a partition CTA
+constexpr int kPartThreads = 512;              // threads of a partition CTA
+constexpr int kPartBlocks = 4;                 // partition CTAs per SM (registers: 32 per thread)
 constexpr int kPartPer = 8;                    // entries per thread per partition CTA
-constexpr int kPartRound = kPartThreads * kPartPer;   // 8192 entries per partition CTA
+constexpr int kPartRound = kPartThreads * kPartPer;   // 4096 entries per partition CTA
 constexpr uint32_t kEsc12 = 0xfffu;            // 12-bit length field of level 1: value in lbig
 constexpr uint32_t kEsc17 = 0x1ffffu;          // 17-bit length field of level 2: value in lbig
 constexpr int kCursorStride = 32;              // one 128-byte line per partition cursor
