@@ -75,8 +75,10 @@ __global__ void k_heads(const uint64_t* __restrict__ key, long long total, int32
         h = (g == 0) || (key[g] != key[g - 1]);
         head[g] = h ? (int32_t)g : 0;
     }
-    const unsigned b = __ballot_sync(0xffffffffu, h);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(groups, (unsigned long long)__popc(b));
+    // one atomic per block: a per-warp add on one counter serialised ~8 M
+    // atomics per round at n = 256 Mi
+    const int cnt = __syncthreads_count(h);
+    if (threadIdx.x == 0 && cnt) atomicAdd(groups, (unsigned long long)cnt);
 }
 
 __global__ void k_scatter_rank(const int32_t* __restrict__ sorted, const int32_t* __restrict__ hp, long long total,

@@ -190,7 +190,21 @@ __global__ void __launch_bounds__(256) k_walk_stats(int32_t n, const int32_t* __
     }
     warp_minmax_sum(a_min, a_max, a_sum);
     warp_minmax_sum(b_min, b_max, b_sum);
-    if ((threadIdx.x & 31) == 0 && a_max >= 0) {
+    // block reduction, then one set of atomics per block
+    __shared__ long long s_a[8], s_b[8];
+    __shared__ int s_v[8][4];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_a[warp] = a_sum; s_b[warp] = b_sum;
+        s_v[warp][0] = a_min; s_v[warp][1] = a_max; s_v[warp][2] = b_min; s_v[warp][3] = b_max;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            a_sum += s_a[w]; b_sum += s_b[w];
+            a_min = min(a_min, s_v[w][0]); a_max = max(a_max, s_v[w][1]);
+            b_min = min(b_min, s_v[w][2]); b_max = max(b_max, s_v[w][3]);
+        }
         atomicAdd(&stats[0], (unsigned long long)a_sum);
         atomicAdd(&stats[1], (unsigned long long)b_sum);
         int* w = reinterpret_cast<int*>(stats + 2);
