@@ -711,7 +711,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="shrink the workload (same seed); default full size")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-step-seconds", type=float, default=4.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=2.0)
     ap.add_argument("--e2e-inflight", type=int, default=3,
                     help="host-buffer queries in flight at once in the e2e measurement")
     ap.add_argument("--batched-count", type=int, default=512,
