@@ -215,6 +215,43 @@ def _event_ms(stream, fn, reps, warm=2):
     return e0.elapsed_time(e1) / reps
 
 
+def host_link(dev, stream, h_in, d_in, h_out, d_out, reps: int = 3):
+    """Host link bandwidth (GB/s) of plain pinned copies on `stream`: host to
+    device (h_in -> d_in), device to host (d_out -> h_out) and both at once on
+    two streams.  The e2e figure cannot beat the slowest of the three for its
+    bytes per step."""
+    import torch
+    s2 = torch.cuda.Stream(dev)
+
+    def h2d():
+        with torch.cuda.stream(stream):
+            d_in.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(stream):
+            h_out.copy_(d_out, non_blocking=True)
+
+    def both():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        s2.wait_event(ev)
+        with torch.cuda.stream(stream):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+        done = torch.cuda.Event()
+        done.record(s2)
+        stream.wait_event(done)
+
+    b_in = h_in.numel() * h_in.element_size()
+    b_out = h_out.numel() * h_out.element_size()
+    out = {"h2d_gbs": round(b_in / (_event_ms(stream, h2d, reps, warm=1) * 1e6), 1),
+           "d2h_gbs": round(b_out / (_event_ms(stream, d2h, reps, warm=1) * 1e6), 1),
+           "duplex_gbs": round((b_in + b_out) / (_event_ms(stream, both, reps, warm=1) * 1e6), 1)}
+    torch.cuda.synchronize(dev)
+    return out
+
+
 def batched_leg(lr, dev, stream, count: int, reps: int):
     """The batched mix (log-uniform lengths 1 Ki - 4 Mi, half DNA with planted
     repeats, half protein with tandem repeats) in one batched query, tuned and
@@ -555,6 +592,12 @@ def run_ours(args):
             raise lr.LRError(s, "lr_query_all_host")
     e2e_single_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_single_ms = max_over_ranks(e2e_single_ms, dev)
+    link = host_link(dev, stream, h_sa, d_sa, h_ln, ln)
+    h2d_step = 4 * n + 4 * (n + 1)                                   # sa + lcp
+    d2h_step = 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8            # lr_len, lr_start, offsets, starts, total
+    link_ms = max(h2d_step / link["h2d_gbs"], d2h_step / link["d2h_gbs"],
+                  (h2d_step + d2h_step) / link["duplex_gbs"]) * 1e-6
+    link["e2e_bound"] = round(whole_job_rate(ws, n, link_ms), 3)
     # the same calls with `inflight` steps at a time (one host thread, context,
     # stream and output buffers each; ctypes releases the GIL), so that one
     # step's device-to-host copies overlap the next one's host-to-device
@@ -657,10 +700,11 @@ def run_ours(args):
                              "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
                                        "[%d, %d) of the same workload, %.1f s single-threaded" % (a0, a0 + block, dt)},
             "e2e": {"value": round(whole_job_rate(ws, n, e2e_ms), 3), "unit": UNIT,
-                    "h2d_bytes_per_step": 4 * n + 4 * (n + 1),   # sa + lcp
-                    "d2h_bytes_per_step": 4 * n + 4 * n + 8 * (n + 1) + 4 * total + 8,
+                    "h2d_bytes_per_step": h2d_step,
+                    "d2h_bytes_per_step": d2h_step,
                     "steps_in_flight": inflight,
                     "one_in_flight": round(whole_job_rate(ws, n, e2e_single_ms), 3),
+                    "host_link": link,
                     "api": "lr_query_all_host (pinned host buffers; copies and kernels inside the call)"},
             "gpu_launches": launches,
             "clocks": clk,
