@@ -17,9 +17,11 @@
 //    strings and the first c * 2^r symbols are;
 //  * rounds stop when all ranks differ: sorted position g holds the suffix of
 //    local rank g - off[j];
-//  * lcp of each pair of sa neighbours by binary lifting over the ranks of
-//    every round (longest first: equal ranks at round r mean c * 2^r equal
-//    symbols, skip them), then fewer than c symbol comparisons.
+//  * lcp of each pair of sa neighbours: the round at which they parted
+//    gives it within a factor of two (first c * 2^(r-1) symbols equal, fewer
+//    than c * 2^r), binary lifting over the ranks of the earlier rounds
+//    (equal ranks at round q mean c * 2^q equal symbols) and fewer than c
+//    symbol comparisons give the rest.
 #include <cuda_runtime.h>
 #include <cub/cub.cuh>
 #include <cstdint>
@@ -66,19 +68,36 @@ __global__ void k_keys(const int32_t* __restrict__ rank, long long total, long l
 }
 
 // head[g] = g where sorted key g starts a group of equal keys, else 0; the
-// number of groups is added to *groups.
-__global__ void k_heads(const uint64_t* __restrict__ key, long long total, int32_t* __restrict__ head,
-                        unsigned long long* __restrict__ groups) {
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool h = false;
-    if (g < total) {
-        h = (g == 0) || (key[g] != key[g - 1]);
-        head[g] = h ? (int32_t)g : 0;
+// number of groups is added to *groups, and sep[g] (0xff until then) takes
+// the first round at which g starts a group.  A block takes kHeadsPer x 256
+// consecutive keys and adds its count with one atomic: adds on the one
+// counter serialise (one per 256 keys cost ~5 ms per round at n = 256 Mi).
+constexpr int kHeadsThreads = 256;
+constexpr int kHeadsPer = 16;
+__global__ void __launch_bounds__(kHeadsThreads)
+k_heads(const uint64_t* __restrict__ key, long long total, int32_t* __restrict__ head,
+        unsigned long long* __restrict__ groups, uint8_t* __restrict__ sep, int round) {
+    __shared__ int wsum[kHeadsThreads / 32];
+    const long long g0 = (long long)blockIdx.x * (kHeadsThreads * kHeadsPer) + threadIdx.x;
+    int cnt = 0;
+#pragma unroll 4
+    for (int u = 0; u < kHeadsPer; ++u) {
+        const long long g = g0 + (long long)u * kHeadsThreads;
+        if (g < total) {
+            const bool h = (g == 0) || (__ldg(key + g) != __ldg(key + g - 1));
+            head[g] = h ? (int32_t)g : 0;
+            cnt += h;
+            if (h && sep[g] == 0xff) sep[g] = (uint8_t)round;   // group boundaries stay where they are
+        }
     }
-    // one atomic per block: a per-warp add on one counter serialised ~8 M
-    // atomics per round at n = 256 Mi
-    const int cnt = __syncthreads_count(h);
-    if (threadIdx.x == 0 && cnt) atomicAdd(groups, (unsigned long long)cnt);
+    cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kHeadsThreads / 32; ++w) t += (unsigned long long)wsum[w];
+        if (t) atomicAdd(groups, t);
+    }
 }
 
 __global__ void k_scatter_rank(const int32_t* __restrict__ sorted, const int32_t* __restrict__ hp, long long total,
@@ -89,24 +108,36 @@ __global__ void k_scatter_rank(const int32_t* __restrict__ sorted, const int32_t
 
 // lcp of sorted neighbours g - 1, g of one string, written in the layout the
 // queries take (string j's n_j + 1 entries at off[j] + j), and the string-
-// local sa and rank.
+// local sa and rank (index g read as a rank for sa, as a position for rank:
+// both lie in string j's range [off[j], off[j+1])).  The two suffixes parted
+// at round r = sep[g]: their first csyms * 2^(r-1) symbols are equal (none
+// for r = 0) and fewer than csyms * 2^r are; the rest is found by binary
+// lifting over the ranks of rounds r - 2 .. 0 (equal ranks at round q mean
+// csyms * 2^q more equal symbols, longest first), then fewer than csyms
+// symbol comparisons.
 __global__ void k_lcp(const uint8_t* __restrict__ text, long long total, const int64_t* __restrict__ off,
                       long long num, const int32_t* __restrict__ sorted, const int32_t* __restrict__ levels,
-                      int rounds, int csyms, const int32_t* __restrict__ end, const int32_t* __restrict__ frank,
+                      int rounds, int csyms, const uint8_t* __restrict__ sep, const int32_t* __restrict__ frank,
                       int32_t* __restrict__ sa, int32_t* __restrict__ rank, int32_t* __restrict__ lcp) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
     const long long j = string_of(off, num, g);
-    const long long a = __ldg(off + j);
+    const long long a = __ldg(off + j), e = __ldg(off + j + 1);
     sa[g] = (int32_t)(sorted[g] - a);
     rank[g] = (int32_t)(frank[g] - a);
     int32_t out = 0;
     if (g > a) {
         long long x = sorted[g - 1], y = sorted[g], l = 0;
-        const long long e = __ldg(end + y);
-        for (int r = rounds - 1; r >= 0; --r) {
-            const long long len = (long long)csyms << r;
-            const int32_t* R = levels + (size_t)r * (size_t)total;
+        int r = sep[g];
+        r = r < rounds ? r : rounds - 1;               // every index parts by the last round
+        if (r > 0) {
+            l = (long long)csyms << (r - 1);
+            x += l;
+            y += l;
+        }
+        for (int q = r - 2; q >= 0; --q) {
+            const long long len = (long long)csyms << q;
+            const int32_t* R = levels + (size_t)q * (size_t)total;
             if (x < e && y < e && __ldg(R + x) == __ldg(R + y)) { l += len; x += len; y += len; }
         }
         for (int t = 0; t < csyms && x < e && y < e && __ldg(text + x) == __ldg(text + y); ++t) { ++l; ++x; ++y; }
@@ -140,12 +171,14 @@ struct MaxOp {
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 size_t sort_temp_bytes(long long n) {
-    size_t a = 0, b = 0;
+    size_t a = 0, b = 0, c = 0;
     cub::DoubleBuffer<uint64_t> keys(nullptr, nullptr);
-    cub::DoubleBuffer<int32_t> vals(nullptr, nullptr);
+    cub::DoubleBuffer<int32_t> vals(nullptr, nullptr), pos(nullptr, nullptr);
     cub::DeviceRadixSort::SortPairs(nullptr, a, keys, vals, (int)n, 0, 64, (cudaStream_t)0);
     cub::DeviceScan::InclusiveScan(nullptr, b, (int32_t*)nullptr, (int32_t*)nullptr, MaxOp{}, (int)n, (cudaStream_t)0);
-    return (a > b ? a : b) + 256;
+    cub::DeviceRadixSort::SortPairs(nullptr, c, pos, vals, (int)n, 0, 32, (cudaStream_t)0);
+    if (b > a) a = b;
+    return (c > a ? c : a) + 256;
 }
 
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -155,7 +188,7 @@ inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 // Layout of the work memory for n positions and `rounds` rank levels.
 size_t index_work_bytes(long long n, int rounds) {
     const size_t nn = (size_t)n;
-    return al(nn * 8) * 2 + al(nn * 4) * 5 + al((size_t)rounds * nn * 4) + al(64) + al(sort_temp_bytes(n));
+    return al(nn * 8) * 2 + al(nn * 4) * 5 + al(nn) + al((size_t)rounds * nn * 4) + al(64) + al(sort_temp_bytes(n));
 }
 
 cudaError_t IndexWork::alloc(long long n, int rounds) {
@@ -172,6 +205,7 @@ cudaError_t IndexWork::alloc(long long n, int rounds) {
     head = (int32_t*)p; p += al(nn * 4);
     hp = (int32_t*)p; p += al(nn * 4);
     end = (int32_t*)p; p += al(nn * 4);
+    sep = (uint8_t*)p; p += al(nn);
     levels = (int32_t*)p; p += al((size_t)rounds * nn * 4);
     misc = (unsigned long long*)p; p += al(64);
     tmp = p;
@@ -219,6 +253,8 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
     while (bits < 31 && (1ll << bits) <= total) ++bits;
     cub::DoubleBuffer<uint64_t> keys(w.k0, w.k1);
     cub::DoubleBuffer<int32_t> vals(w.v0, w.v1);
+    e = cudaMemsetAsync(w.sep, 0xff, nn, stream);
+    if (e != cudaSuccess) return e;
     int r = 0;
     for (;; ++r) {
         if (r >= 40) return cudaErrorUnknown;
@@ -230,6 +266,7 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
             e = cudaMemcpyAsync(bigger.levels, w.levels, (size_t)w.cap_rounds * nn * 4, cudaMemcpyDeviceToDevice,
                                 stream);
             if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.end, w.end, nn * 4, cudaMemcpyDeviceToDevice, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.sep, w.sep, nn, cudaMemcpyDeviceToDevice, stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
             if (e != cudaSuccess) { bigger.release(); return e; }
             w.release();
@@ -253,19 +290,33 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
         e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, end_bit, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 8, stream);
         if (e != cudaSuccess) return e;
-        k_heads<<<blocks(total, 256), 256, 0, stream>>>(keys.Current(), total, w.head, w.misc);
+        k_heads<<<blocks(total, kHeadsThreads * kHeadsPer), kHeadsThreads, 0, stream>>>(keys.Current(), total,
+                                                                                      w.head, w.misc, w.sep, r);
         tb = w.tmp_bytes;
         e = cub::DeviceScan::InclusiveScan(w.tmp, tb, w.head, w.hp, MaxOp{}, (int)total, stream);
-        if (e != cudaSuccess) return e;
-        k_scatter_rank<<<blocks(total, 256), 256, 0, stream>>>(vals.Current(), w.hp, total, w.levels + (size_t)r * nn);
-        e = cudaMemcpyAsync(&w.groups_host, w.misc, 8, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&w.groups_host, w.misc, 8, cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return e;
-        if (w.groups_host == (unsigned long long)total) break;
+        int32_t* level = w.levels + (size_t)r * nn;
+        if (w.groups_host == (unsigned long long)total) {
+            // last round: the sorted positions are the suffix array, keep them
+            k_scatter_rank<<<blocks(total, 256), 256, 0, stream>>>(vals.Current(), w.hp, total, level);
+            break;
+        }
+        // the ranks back in position order by a radix sort keyed by position
+        // (streaming passes instead of one random 4-byte store per position);
+        // the sorted positions are not needed again
+        cub::DoubleBuffer<int32_t> pos(vals.Current(), vals.Alternate());
+        cub::DoubleBuffer<int32_t> rnk(w.hp, level);
+        tb = w.tmp_bytes;
+        e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, pos, rnk, (int)total, 0, bits, stream);
+        if (e == cudaSuccess && rnk.Current() != level)
+            e = cudaMemcpyAsync(level, rnk.Current(), nn * 4, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return e;
     }
     const int rounds = r + 1;
     k_lcp<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, vals.Current(), w.levels, rounds, csyms,
-                                                  w.end, w.levels + (size_t)r * nn, sa, rank, lcp);
+                                                  w.sep, w.levels + (size_t)r * nn, sa, rank, lcp);
     if (rounds_out) *rounds_out = rounds;
     return cudaGetLastError();
 }

@@ -119,6 +119,7 @@ struct IndexWork {
     size_t bytes = 0;
     uint64_t *k0 = nullptr, *k1 = nullptr;
     int32_t *v0 = nullptr, *v1 = nullptr, *head = nullptr, *hp = nullptr, *end = nullptr, *levels = nullptr;
+    uint8_t* sep = nullptr;        // per sorted index: the round at which it started a group
     unsigned long long* misc = nullptr;
     void* tmp = nullptr;
     size_t tmp_bytes = 0;
