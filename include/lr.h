@@ -140,7 +140,8 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
  * built in parallel on the GPU by prefix doubling (Sec. 4); these calls do
  * that: radix sorts of (string index, first symbols) keys, then of
  * (rank(i), rank(i + h)) pairs for doubling h until all ranks differ, and
- * the lcp of sa neighbours by binary lifting over the ranks of every round.
+ * the lcp of sa neighbours from the round at which they parted plus binary
+ * lifting over the ranks of the earlier rounds.
  *
  * lr_build_arrays: one string, d_text n bytes (any values); outputs in the
  * layout the queries take: d_sa and d_rank n entries, d_lcp n + 1
