@@ -58,25 +58,30 @@ __global__ void k_keys0(const uint8_t* __restrict__ text, long long total, const
     end[i] = (int32_t)e;
 }
 
-__global__ void k_keys(const int32_t* __restrict__ rank, long long total, long long h, const int32_t* __restrict__ end,
-                       uint64_t* __restrict__ key, int32_t* __restrict__ val) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
+// Round r >= 1 keys of the suffixes still in groups of two or more (act[0..A)):
+// (rank(i), rank(i + h) + 1, or 0 past the end of i's string).
+__global__ void k_keys_act(const int32_t* __restrict__ act, long long A, const int32_t* __restrict__ rank,
+                           long long h, const int32_t* __restrict__ end, uint64_t* __restrict__ key,
+                           int32_t* __restrict__ val) {
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A) return;
+    const long long i = __ldg(act + a);
     const uint32_t second = (i + h < __ldg(end + i)) ? (uint32_t)__ldg(rank + i + h) + 1u : 0u;
-    key[i] = ((uint64_t)(uint32_t)__ldg(rank + i) << 32) | second;
-    val[i] = (int32_t)i;
+    key[a] = ((uint64_t)(uint32_t)__ldg(rank + i) << 32) | second;
+    val[a] = (int32_t)i;
 }
 
-// head[g] = g where sorted key g starts a group of equal keys, else 0; the
-// number of groups is added to *groups, and sep[g] (0xff until then) takes
-// the first round at which g starts a group.  A block takes kHeadsPer x 256
-// consecutive keys and adds its count with one atomic: adds on the one
-// counter serialise (one per 256 keys cost ~5 ms per round at n = 256 Mi).
+// Round 0, over all sorted keys: head[g] = g where key g starts a group of
+// equal keys, else 0; the number of groups is added to *groups; sep[g] = 0
+// where g starts a group; flags[g] = 1 where g is in a group of two or
+// more.  A block takes kHeadsPer x 256 consecutive keys and adds its count
+// with one atomic: adds on the one counter serialise (one per 256 keys cost
+// ~5 ms at n = 256 Mi).
 constexpr int kHeadsThreads = 256;
 constexpr int kHeadsPer = 16;
 __global__ void __launch_bounds__(kHeadsThreads)
 k_heads(const uint64_t* __restrict__ key, long long total, int32_t* __restrict__ head,
-        unsigned long long* __restrict__ groups, uint8_t* __restrict__ sep, int round) {
+        unsigned long long* __restrict__ groups, uint8_t* __restrict__ sep, uint8_t* __restrict__ flags) {
     __shared__ int wsum[kHeadsThreads / 32];
     const long long g0 = (long long)blockIdx.x * (kHeadsThreads * kHeadsPer) + threadIdx.x;
     int cnt = 0;
@@ -84,10 +89,12 @@ k_heads(const uint64_t* __restrict__ key, long long total, int32_t* __restrict__
     for (int u = 0; u < kHeadsPer; ++u) {
         const long long g = g0 + (long long)u * kHeadsThreads;
         if (g < total) {
-            const bool h = (g == 0) || (__ldg(key + g) != __ldg(key + g - 1));
+            const uint64_t k = __ldg(key + g);
+            const bool h = (g == 0) || (k != __ldg(key + g - 1));
             head[g] = h ? (int32_t)g : 0;
             cnt += h;
-            if (h && sep[g] == 0xff) sep[g] = (uint8_t)round;   // group boundaries stay where they are
+            if (h) sep[g] = 0;
+            flags[g] = !h || (g + 1 < total && __ldg(key + g + 1) == k);
         }
     }
     cnt = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
@@ -104,6 +111,48 @@ __global__ void k_scatter_rank(const int32_t* __restrict__ sorted, const int32_t
                                int32_t* __restrict__ rank) {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g < total) rank[sorted[g]] = hp[g];
+}
+
+// Round r >= 1, over the re-sorted keys key[0..A): mh[a] = a where key a
+// starts a new group, mo[a] = a where it starts a group of the previous
+// round (its first half, the old rank, changes); else 0.
+__global__ void k_marks(const uint64_t* __restrict__ key, long long A, int32_t* __restrict__ mh,
+                        int32_t* __restrict__ mo) {
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A) return;
+    const uint64_t k = __ldg(key + a);
+    bool nh = true, oh = true;
+    if (a > 0) {
+        const uint64_t p = __ldg(key + a - 1);
+        nh = k != p;
+        oh = (k >> 32) != (p >> 32);
+    }
+    mh[a] = nh ? (int32_t)a : 0;
+    mo[a] = oh ? (int32_t)a : 0;
+}
+
+// Round r >= 1: an old group (rank g0 = its first sorted index) holds its
+// re-sorted members at a0 .. a0 + size - 1, so member a sits at sorted index
+// g0 + a - a0 and its new rank is the index of its new group's first member,
+// g0 + ah - a0 (ah, a0: max-scans of the marks).  New group starts inside an
+// old group take sep = r; members still in groups of two or more are
+// flagged for the next round.
+__global__ void k_update(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                         const int32_t* __restrict__ ah, const int32_t* __restrict__ a0, long long A,
+                         int32_t* __restrict__ rank, uint8_t* __restrict__ sep, int round,
+                         uint8_t* __restrict__ flags) {
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A) return;
+    const uint64_t k = __ldg(key + a);
+    const long long g0 = (long long)(k >> 32), s0 = __ldg(a0 + a), hh = __ldg(ah + a);
+    rank[__ldg(val + a)] = (int32_t)(g0 + (hh - s0));
+    if (hh == a && s0 != a) sep[g0 + (a - s0)] = (uint8_t)round;
+    flags[a] = (a > 0 && __ldg(key + a - 1) == k) || (a + 1 < A && __ldg(key + a + 1) == k);
+}
+
+__global__ void k_iota(int32_t* __restrict__ v, long long total) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total) v[i] = (int32_t)i;
 }
 
 // lcp of sorted neighbours g - 1, g of one string, written in the layout the
@@ -177,7 +226,11 @@ size_t sort_temp_bytes(long long n) {
     cub::DeviceRadixSort::SortPairs(nullptr, a, keys, vals, (int)n, 0, 64, (cudaStream_t)0);
     cub::DeviceScan::InclusiveScan(nullptr, b, (int32_t*)nullptr, (int32_t*)nullptr, MaxOp{}, (int)n, (cudaStream_t)0);
     cub::DeviceRadixSort::SortPairs(nullptr, c, pos, vals, (int)n, 0, 32, (cudaStream_t)0);
+    size_t d = 0;
+    cub::DeviceSelect::Flagged(nullptr, d, (const int32_t*)nullptr, (const uint8_t*)nullptr, (int32_t*)nullptr,
+                               (unsigned long long*)nullptr, (int)n, (cudaStream_t)0);
     if (b > a) a = b;
+    if (d > a) a = d;
     return (c > a ? c : a) + 256;
 }
 
@@ -254,69 +307,111 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
     cub::DoubleBuffer<uint64_t> keys(w.k0, w.k1);
     cub::DoubleBuffer<int32_t> vals(w.v0, w.v1);
     e = cudaMemsetAsync(w.sep, 0xff, nn, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 24, stream);
     if (e != cudaSuccess) return e;
-    int r = 0;
-    for (;; ++r) {
-        if (r >= 40) return cudaErrorUnknown;
-        if (r >= w.cap_rounds) {                          // more rounds than the level store holds
-            if (!grow) return cudaErrorMemoryAllocation;
-            IndexWork bigger;
-            e = bigger.alloc(w.cap_n, w.cap_rounds * 2);
+    // round 0: every suffix by its string and first csyms symbols
+    k_keys0<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, csyms, keys.Current(), vals.Current(),
+                                                    w.end);
+    size_t tb = w.tmp_bytes;
+    e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, jobbits + 9 * csyms, stream);
+    if (e != cudaSuccess) return e;
+    uint8_t* flags = reinterpret_cast<uint8_t*>(keys.Alternate());
+    k_heads<<<blocks(total, kHeadsThreads * kHeadsPer), kHeadsThreads, 0, stream>>>(keys.Current(), total, w.head,
+                                                                                  w.misc, w.sep, flags);
+    tb = w.tmp_bytes;
+    e = cub::DeviceScan::InclusiveScan(w.tmp, tb, w.head, w.hp, MaxOp{}, (int)total, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&w.groups_host, w.misc, 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    int rounds = 1;
+    const int32_t* sorted = nullptr;                       // the suffix array (flattened) at the end
+    if (w.groups_host == (unsigned long long)total) {
+        // all first keys differ: the sorted positions are the suffix array
+        k_scatter_rank<<<blocks(total, 256), 256, 0, stream>>>(vals.Current(), w.hp, total, w.levels);
+        sorted = vals.Current();
+    } else {
+        // the suffixes in groups of two or more (act, in w.head) are the only
+        // ones sorted again; then the ranks go back to position order by a
+        // radix sort keyed by position (streaming passes instead of one random
+        // 4-byte store per position)
+        long long A = 0;
+        tb = w.tmp_bytes;
+        e = cub::DeviceSelect::Flagged(w.tmp, tb, vals.Current(), flags, w.head, w.misc + 2, (int)total, stream);
+        if (e != cudaSuccess) return e;
+        {
+            cub::DoubleBuffer<int32_t> pos(vals.Current(), vals.Alternate());
+            cub::DoubleBuffer<int32_t> rnk(w.hp, w.levels);
+            tb = w.tmp_bytes;
+            e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, pos, rnk, (int)total, 0, bits, stream);
+            if (e == cudaSuccess && rnk.Current() != w.levels)
+                e = cudaMemcpyAsync(w.levels, rnk.Current(), nn * 4, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return e;
-            e = cudaMemcpyAsync(bigger.levels, w.levels, (size_t)w.cap_rounds * nn * 4, cudaMemcpyDeviceToDevice,
-                                stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.end, w.end, nn * 4, cudaMemcpyDeviceToDevice, stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.sep, w.sep, nn, cudaMemcpyDeviceToDevice, stream);
+        }
+        for (int r = 1;; ++r) {
+            e = cudaMemcpyAsync(&w.groups_host, w.misc + 2, 8, cudaMemcpyDeviceToHost, stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-            if (e != cudaSuccess) { bigger.release(); return e; }
-            w.release();
-            w = bigger;
-            bigger.base = nullptr;                        // owned by w now
-            keys = cub::DoubleBuffer<uint64_t>(w.k0, w.k1);
-            vals = cub::DoubleBuffer<int32_t>(w.v0, w.v1);
-        }
-        int end_bit;
-        if (r == 0) {
-            k_keys0<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, csyms, keys.Current(),
-                                                            vals.Current(), w.end);
-            end_bit = jobbits + 9 * csyms;
-        } else {
+            if (e != cudaSuccess) return e;
+            A = (long long)w.groups_host;
+            if (A == 0) { rounds = r; break; }
+            if (r >= 40 || A > total) return cudaErrorUnknown;
+            if (r >= w.cap_rounds) {                          // more rounds than the level store holds
+                if (!grow) return cudaErrorMemoryAllocation;
+                IndexWork bigger;
+                e = bigger.alloc(w.cap_n, w.cap_rounds * 2);
+                if (e != cudaSuccess) return e;
+                e = cudaMemcpyAsync(bigger.levels, w.levels, (size_t)w.cap_rounds * nn * 4, cudaMemcpyDeviceToDevice,
+                                    stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.end, w.end, nn * 4, cudaMemcpyDeviceToDevice, stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.sep, w.sep, nn, cudaMemcpyDeviceToDevice, stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(bigger.head, w.head, (size_t)A * 4, cudaMemcpyDeviceToDevice,
+                                                          stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+                if (e != cudaSuccess) { bigger.release(); return e; }
+                w.release();
+                w = bigger;
+                bigger.base = nullptr;                        // owned by w now
+                keys = cub::DoubleBuffer<uint64_t>(w.k0, w.k1);
+                vals = cub::DoubleBuffer<int32_t>(w.v0, w.v1);
+            }
+            const int32_t* prev = w.levels + (size_t)(r - 1) * nn;
+            int32_t* level = w.levels + (size_t)r * nn;
+            e = cudaMemcpyAsync(level, prev, nn * 4, cudaMemcpyDeviceToDevice, stream);   // settled ranks stay
+            if (e != cudaSuccess) return e;
             const long long h = (long long)csyms << (r - 1);
-            k_keys<<<blocks(total, 256), 256, 0, stream>>>(w.levels + (size_t)(r - 1) * nn, total, h, w.end,
-                                                           keys.Current(), vals.Current());
-            end_bit = 32 + bits;
+            k_keys_act<<<blocks(A, 256), 256, 0, stream>>>(w.head, A, prev, h, w.end, keys.Current(), vals.Current());
+            tb = w.tmp_bytes;
+            e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)A, 0, 32 + bits, stream);
+            if (e != cudaSuccess) return e;
+            int32_t* mh = reinterpret_cast<int32_t*>(keys.Alternate());
+            int32_t* mo = mh + nn;
+            int32_t* a0 = vals.Alternate();
+            k_marks<<<blocks(A, 256), 256, 0, stream>>>(keys.Current(), A, mh, mo);
+            tb = w.tmp_bytes;
+            e = cub::DeviceScan::InclusiveScan(w.tmp, tb, mh, w.hp, MaxOp{}, (int)A, stream);
+            tb = w.tmp_bytes;
+            if (e == cudaSuccess) e = cub::DeviceScan::InclusiveScan(w.tmp, tb, mo, a0, MaxOp{}, (int)A, stream);
+            if (e != cudaSuccess) return e;
+            flags = reinterpret_cast<uint8_t*>(keys.Alternate());
+            k_update<<<blocks(A, 256), 256, 0, stream>>>(keys.Current(), vals.Current(), w.hp, a0, A, level, w.sep, r,
+                                                         flags);
+            tb = w.tmp_bytes;
+            e = cub::DeviceSelect::Flagged(w.tmp, tb, vals.Current(), flags, w.head, w.misc + 2, (int)A, stream);
+            if (e != cudaSuccess) return e;
         }
-        size_t tb = w.tmp_bytes;
-        e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, end_bit, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 8, stream);
+        // the suffix array: positions sorted by their final (distinct) ranks
+        int32_t* kk = reinterpret_cast<int32_t*>(w.k0);
+        e = cudaMemcpyAsync(kk, w.levels + (size_t)(rounds - 1) * nn, nn * 4, cudaMemcpyDeviceToDevice, stream);
         if (e != cudaSuccess) return e;
-        k_heads<<<blocks(total, kHeadsThreads * kHeadsPer), kHeadsThreads, 0, stream>>>(keys.Current(), total,
-                                                                                      w.head, w.misc, w.sep, r);
+        k_iota<<<blocks(total, 256), 256, 0, stream>>>(w.v0, total);
+        cub::DoubleBuffer<int32_t> fk(kk, kk + nn);
+        cub::DoubleBuffer<int32_t> fv(w.v0, w.v1);
         tb = w.tmp_bytes;
-        e = cub::DeviceScan::InclusiveScan(w.tmp, tb, w.head, w.hp, MaxOp{}, (int)total, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&w.groups_host, w.misc, 8, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, fk, fv, (int)total, 0, bits, stream);
         if (e != cudaSuccess) return e;
-        int32_t* level = w.levels + (size_t)r * nn;
-        if (w.groups_host == (unsigned long long)total) {
-            // last round: the sorted positions are the suffix array, keep them
-            k_scatter_rank<<<blocks(total, 256), 256, 0, stream>>>(vals.Current(), w.hp, total, level);
-            break;
-        }
-        // the ranks back in position order by a radix sort keyed by position
-        // (streaming passes instead of one random 4-byte store per position);
-        // the sorted positions are not needed again
-        cub::DoubleBuffer<int32_t> pos(vals.Current(), vals.Alternate());
-        cub::DoubleBuffer<int32_t> rnk(w.hp, level);
-        tb = w.tmp_bytes;
-        e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, pos, rnk, (int)total, 0, bits, stream);
-        if (e == cudaSuccess && rnk.Current() != level)
-            e = cudaMemcpyAsync(level, rnk.Current(), nn * 4, cudaMemcpyDeviceToDevice, stream);
-        if (e != cudaSuccess) return e;
+        sorted = fv.Current();
     }
-    const int rounds = r + 1;
-    k_lcp<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, vals.Current(), w.levels, rounds, csyms,
-                                                  w.sep, w.levels + (size_t)r * nn, sa, rank, lcp);
+    k_lcp<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, sorted, w.levels, rounds, csyms, w.sep,
+                                                  w.levels + (size_t)(rounds - 1) * nn, sa, rank, lcp);
     if (rounds_out) *rounds_out = rounds;
     return cudaGetLastError();
 }
