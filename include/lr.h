@@ -139,7 +139,8 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
  * GPU.  The paper builds these arrays on the host and notes they could be
  * built in parallel on the GPU by prefix doubling (Sec. 4); these calls do
  * that: radix sorts of (string index, first symbols) keys, then of
- * (rank(i), rank(i + h)) pairs for doubling h until all ranks differ, and
+ * (rank(i), rank(i + h)) pairs of the suffixes not yet told apart, for
+ * doubling h until all ranks differ, and
  * the lcp of sa neighbours from the round at which they parted plus binary
  * lifting over the ranks of the earlier rounds.
  *
