@@ -13,10 +13,14 @@
 //    own (a max-scan over group heads).  Strings occupy consecutive rank
 //    ranges, [off[j], off[j+1]) for string j;
 //  * round r >= 1, h = c * 2^(r-1): key(i) = (rank(i), rank(i + h) + 1, or 0
-//    past the end of i's string), sorted again; ranks are equal iff the
-//    strings and the first c * 2^r symbols are;
-//  * rounds stop when all ranks differ: sorted position g holds the suffix of
-//    local rank g - off[j];
+//    past the end of i's string), for the suffixes still in groups of two or
+//    more only (the others keep their ranks), sorted again; ranks are equal
+//    iff the strings and the first c * 2^r symbols are; a re-sorted suffix
+//    takes the rank of its old group's start plus the offset of its new
+//    group inside the old one;
+//  * rounds stop when all ranks differ; the suffix array is the positions
+//    sorted by rank (flattened index g holds the suffix of local rank
+//    g - off[j]);
 //  * lcp of each pair of sa neighbours: the round at which they parted
 //    gives it within a factor of two (first c * 2^(r-1) symbols equal, fewer
 //    than c * 2^r), binary lifting over the ranks of the earlier rounds
