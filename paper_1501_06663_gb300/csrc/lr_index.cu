@@ -28,6 +28,7 @@
 //    symbol comparisons give the rest.
 #include <cuda_runtime.h>
 #include <cub/cub.cuh>
+#include <thrust/iterator/counting_iterator.h>
 #include <cstdint>
 #include "lr_internal.h"
 
@@ -62,18 +63,32 @@ __global__ void k_keys0(const uint8_t* __restrict__ text, long long total, const
     end[i] = (int32_t)e;
 }
 
-// Round r >= 1 keys of the suffixes still in groups of two or more (act[0..A)):
-// (rank(i), rank(i + h) + 1, or 0 past the end of i's string).
+// A rank word holds the rank in bits 0..30 and, in bit 31, whether the
+// position is still in a group of two or more (then every member of its
+// group is, so equal words still mean equal groups).
+constexpr uint32_t kActiveBit = 0x80000000u;
+constexpr uint32_t kRankMask = 0x7fffffffu;
+
+// Round r >= 1 keys of the suffixes still in groups of two or more (act[0..A),
+// ascending positions): (rank(i), rank(i + h) + 1, or 0 past the end of i's
+// string).
 __global__ void k_keys_act(const int32_t* __restrict__ act, long long A, const int32_t* __restrict__ rank,
                            long long h, const int32_t* __restrict__ end, uint64_t* __restrict__ key,
                            int32_t* __restrict__ val) {
     const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A) return;
     const long long i = __ldg(act + a);
-    const uint32_t second = (i + h < __ldg(end + i)) ? (uint32_t)__ldg(rank + i + h) + 1u : 0u;
-    key[a] = ((uint64_t)(uint32_t)__ldg(rank + i) << 32) | second;
+    const uint32_t second =
+        (i + h < __ldg(end + i)) ? ((uint32_t)__ldg(rank + i + h) & kRankMask) + 1u : 0u;
+    key[a] = ((uint64_t)((uint32_t)__ldg(rank + i) & kRankMask) << 32) | second;
     val[a] = (int32_t)i;
 }
+
+// Selects position i when its rank word carries the active bit.
+struct ActiveAt {
+    const int32_t* rank;
+    __device__ __forceinline__ bool operator()(int32_t i) const { return ((uint32_t)__ldg(rank + i) & kActiveBit) != 0; }
+};
 
 // Round 0, over all sorted keys: head[g] = g where key g starts a group of
 // equal keys, else 0; the number of groups is added to *groups; sep[g] = 0
@@ -138,20 +153,26 @@ __global__ void k_marks(const uint64_t* __restrict__ key, long long A, int32_t* 
 // Round r >= 1: an old group (rank g0 = its first sorted index) holds its
 // re-sorted members at a0 .. a0 + size - 1, so member a sits at sorted index
 // g0 + a - a0 and its new rank is the index of its new group's first member,
-// g0 + ah - a0 (ah, a0: max-scans of the marks).  New group starts inside an
-// old group take sep = r; members still in groups of two or more are
-// flagged for the next round.
+// g0 + ah - a0 (ah, a0: max-scans of the marks), with the active bit when
+// the new group has two or more members.  New group starts inside an old
+// group take sep = r.
 __global__ void k_update(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
                          const int32_t* __restrict__ ah, const int32_t* __restrict__ a0, long long A,
-                         int32_t* __restrict__ rank, uint8_t* __restrict__ sep, int round,
-                         uint8_t* __restrict__ flags) {
+                         int32_t* __restrict__ rank, uint8_t* __restrict__ sep, int round) {
     const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= A) return;
     const uint64_t k = __ldg(key + a);
     const long long g0 = (long long)(k >> 32), s0 = __ldg(a0 + a), hh = __ldg(ah + a);
-    rank[__ldg(val + a)] = (int32_t)(g0 + (hh - s0));
+    const bool act = (a > 0 && __ldg(key + a - 1) == k) || (a + 1 < A && __ldg(key + a + 1) == k);
+    rank[__ldg(val + a)] = (int32_t)((uint32_t)(g0 + (hh - s0)) | (act ? kActiveBit : 0u));
     if (hh == a && s0 != a) sep[g0 + (a - s0)] = (uint8_t)round;
-    flags[a] = (a > 0 && __ldg(key + a - 1) == k) || (a + 1 < A && __ldg(key + a + 1) == k);
+}
+
+// Round 0: the active bit on the ranks (in sorted order) of keys in groups
+// of two or more.
+__global__ void k_mark_active(int32_t* __restrict__ hp, const uint8_t* __restrict__ flags, long long total) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < total && flags[g]) hp[g] = (int32_t)((uint32_t)hp[g] | kActiveBit);
 }
 
 __global__ void k_iota(int32_t* __restrict__ v, long long total) {
@@ -231,8 +252,8 @@ size_t sort_temp_bytes(long long n) {
     cub::DeviceScan::InclusiveScan(nullptr, b, (int32_t*)nullptr, (int32_t*)nullptr, MaxOp{}, (int)n, (cudaStream_t)0);
     cub::DeviceRadixSort::SortPairs(nullptr, c, pos, vals, (int)n, 0, 32, (cudaStream_t)0);
     size_t d = 0;
-    cub::DeviceSelect::Flagged(nullptr, d, (const int32_t*)nullptr, (const uint8_t*)nullptr, (int32_t*)nullptr,
-                               (unsigned long long*)nullptr, (int)n, (cudaStream_t)0);
+    cub::DeviceSelect::If(nullptr, d, thrust::counting_iterator<int32_t>(0), (int32_t*)nullptr,
+                          (unsigned long long*)nullptr, (int)n, ActiveAt{nullptr}, (cudaStream_t)0);
     if (b > a) a = b;
     if (d > a) a = d;
     return (c > a ? c : a) + 256;
@@ -339,9 +360,7 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
         // radix sort keyed by position (streaming passes instead of one random
         // 4-byte store per position)
         long long A = 0;
-        tb = w.tmp_bytes;
-        e = cub::DeviceSelect::Flagged(w.tmp, tb, vals.Current(), flags, w.head, w.misc + 2, (int)total, stream);
-        if (e != cudaSuccess) return e;
+        k_mark_active<<<blocks(total, 256), 256, 0, stream>>>(w.hp, flags, total);
         {
             cub::DoubleBuffer<int32_t> pos(vals.Current(), vals.Alternate());
             cub::DoubleBuffer<int32_t> rnk(w.hp, w.levels);
@@ -351,6 +370,11 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
                 e = cudaMemcpyAsync(w.levels, rnk.Current(), nn * 4, cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return e;
         }
+        // the active positions, ascending (their rank words are then read in order)
+        tb = w.tmp_bytes;
+        e = cub::DeviceSelect::If(w.tmp, tb, thrust::counting_iterator<int32_t>(0), w.head, w.misc + 2, (int)total,
+                                  ActiveAt{w.levels}, stream);
+        if (e != cudaSuccess) return e;
         for (int r = 1;; ++r) {
             e = cudaMemcpyAsync(&w.groups_host, w.misc + 2, 8, cudaMemcpyDeviceToHost, stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -395,11 +419,10 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
             tb = w.tmp_bytes;
             if (e == cudaSuccess) e = cub::DeviceScan::InclusiveScan(w.tmp, tb, mo, a0, MaxOp{}, (int)A, stream);
             if (e != cudaSuccess) return e;
-            flags = reinterpret_cast<uint8_t*>(keys.Alternate());
-            k_update<<<blocks(A, 256), 256, 0, stream>>>(keys.Current(), vals.Current(), w.hp, a0, A, level, w.sep, r,
-                                                         flags);
+            k_update<<<blocks(A, 256), 256, 0, stream>>>(keys.Current(), vals.Current(), w.hp, a0, A, level, w.sep, r);
             tb = w.tmp_bytes;
-            e = cub::DeviceSelect::Flagged(w.tmp, tb, vals.Current(), flags, w.head, w.misc + 2, (int)A, stream);
+            e = cub::DeviceSelect::If(w.tmp, tb, thrust::counting_iterator<int32_t>(0), w.head, w.misc + 2,
+                                      (int)total, ActiveAt{level}, stream);
             if (e != cudaSuccess) return e;
         }
         // the suffix array: positions sorted by their final (distinct) ranks
