@@ -6,8 +6,10 @@
 // positions [off[j], off[j+1])) in one pass.
 //
 //  * round 0: every suffix gets a key of its string index (most significant)
-//    and its first c symbols (9 bits each, symbol + 1, 0 past the end of its
-//    string; c = 7 for one string, fewer when the string index needs bits);
+//    and its first c symbols, each in the bits its dense code needs (the
+//    symbols that occur numbered 1 .. sigma, 0 past the end of its string;
+//    c = 21 for DNA, 9 for 96 symbols, 7 for all 256, fewer when the string
+//    index needs bits);
 //    the keys are sorted with their positions (radix sort) and each
 //    position's rank becomes the sorted index of the first key equal to its
 //    own (a max-scan over group heads).  Strings occupy consecutive rank
@@ -46,17 +48,38 @@ __device__ __forceinline__ long long string_of(const int64_t* __restrict__ off, 
     return lo;
 }
 
+// The symbols that occur: seen[c] = 1 for every byte value c of the text.
+__global__ void k_seen(const uint8_t* __restrict__ text, long long total, uint8_t* __restrict__ seen) {
+    __shared__ uint8_t s[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s[t] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        s[__ldg(text + i)] = 1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (s[t]) seen[t] = 1;
+}
+
+// Dense codes 1 .. sigma of the symbols that occur (0: past the end of a
+// string), bps bits each.
+struct SymCodes {
+    uint16_t code[256];
+};
+
 __global__ void k_keys0(const uint8_t* __restrict__ text, long long total, const int64_t* __restrict__ off,
-                        long long num, int csyms, uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                        int32_t* __restrict__ end) {
+                        long long num, int csyms, int bps, SymCodes codes, uint64_t* __restrict__ key,
+                        int32_t* __restrict__ val, int32_t* __restrict__ end) {
+    __shared__ uint16_t sc[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) sc[t] = codes.code[t];
+    __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const long long j = string_of(off, num, i);
     const long long e = __ldg(off + j + 1);
     uint64_t k = (uint64_t)j;
     for (int t = 0; t < csyms; ++t) {
-        const uint32_t c = (i + t < e) ? (uint32_t)__ldg(text + i + t) + 1u : 0u;
-        k = (k << 9) | c;
+        const uint32_t c = (i + t < e) ? (uint32_t)sc[__ldg(text + i + t)] : 0u;
+        k = (k << bps) | c;
     }
     key[i] = k;
     val[i] = (int32_t)i;
@@ -324,9 +347,24 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
         return cudaGetLastError();
     }
     const size_t nn = (size_t)total;
+    // the alphabet that occurs, coded densely: more symbols per round-0 key
+    // for a small alphabet (21 for DNA, 9 for 96 symbols, 7 for all 256)
+    uint8_t* seen = reinterpret_cast<uint8_t*>(w.head);
+    e = cudaMemsetAsync(seen, 0, 256, stream);
+    if (e != cudaSuccess) return e;
+    k_seen<<<(unsigned)(total < (1 << 22) ? blocks(total, 256) : 1216), 256, 0, stream>>>(text, total, seen);
+    uint8_t seen_h[256];
+    e = cudaMemcpyAsync(seen_h, seen, 256, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return e;
+    SymCodes codes;
+    int sigma = 0;
+    for (int c = 0; c < 256; ++c) codes.code[c] = seen_h[c] ? (uint16_t)++sigma : (uint16_t)0;
+    int bps = 1;
+    while ((1 << bps) <= sigma) ++bps;                     // codes 0 .. sigma
     int jobbits = 0;
     while (jobbits < 40 && (1ll << jobbits) < num) ++jobbits;
-    const int csyms = (63 - jobbits) / 9;
+    const int csyms = (63 - jobbits) / bps;
     int bits = 1;
     while (bits < 31 && (1ll << bits) <= total) ++bits;
     cub::DoubleBuffer<uint64_t> keys(w.k0, w.k1);
@@ -335,10 +373,10 @@ cudaError_t build_arrays_batch(const uint8_t* text, long long total, const int64
     if (e == cudaSuccess) e = cudaMemsetAsync(w.misc, 0, 24, stream);
     if (e != cudaSuccess) return e;
     // round 0: every suffix by its string and first csyms symbols
-    k_keys0<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, csyms, keys.Current(), vals.Current(),
-                                                    w.end);
+    k_keys0<<<blocks(total, 256), 256, 0, stream>>>(text, total, off, num, csyms, bps, codes, keys.Current(),
+                                                    vals.Current(), w.end);
     size_t tb = w.tmp_bytes;
-    e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, jobbits + 9 * csyms, stream);
+    e = cub::DeviceRadixSort::SortPairs(w.tmp, tb, keys, vals, (int)total, 0, jobbits + bps * csyms, stream);
     if (e != cudaSuccess) return e;
     uint8_t* flags = reinterpret_cast<uint8_t*>(keys.Alternate());
     k_heads<<<blocks(total, kHeadsThreads * kHeadsPer), kHeadsThreads, 0, stream>>>(keys.Current(), total, w.head,

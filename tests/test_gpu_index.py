@@ -38,6 +38,20 @@ def test_small_and_special(ctx):
         _check(ctx, rng.integers(0, sigma, n).astype(np.uint8) * 51)
 
 
+def test_alphabet_sizes(ctx):
+    """Round-0 keys code the symbols that occur densely (more of them per key
+    for a small alphabet): sizes at the code-width boundaries, all 256 byte
+    values included, with a planted repeat so that later rounds run."""
+    rng = np.random.default_rng(10)
+    for sigma in (1, 2, 3, 4, 7, 8, 15, 16, 127, 128, 255, 256):
+        syms = rng.permutation(256)[:sigma].astype(np.uint8)
+        n = int(rng.integers(3000, 7000))
+        text = syms[rng.integers(0, sigma, n)]
+        text[:sigma] = syms                                  # every symbol occurs
+        text[n // 2:n // 2 + 700] = text[300:1000]
+        _check(ctx, text)
+
+
 def test_long_repeats(ctx):
     """a^n and a long tandem need many doubling rounds."""
     _check(ctx, np.full(100000, 97, np.uint8))
