@@ -153,7 +153,8 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
  * lcp (n_j + 1 entries) at d_lcp + d_off[j] + j (total + num entries).
  *
  * Work memory, about (37 + 4 R) bytes per position for R doubling rounds
- * (R is about log2 of the longest repeat / 7, plus 2), is kept in the
+ * (R is about log2 of the longest repeat / c, plus 2, c = 7 .. 63 symbols
+ * per round-0 key by the alphabet size), is kept in the
  * context and grown on demand (LR_ERR_NOMEM when it does not fit).  Both
  * calls wait for `stream` (once per round); *rounds (may be NULL) receives R.
  * An offset table that does not start at 0, end at total or never
