@@ -530,6 +530,8 @@ k_part2(int32_t n, Scratch s) {
 // bucket's place in LLRc by look-back (K3).  Each warp owns a contiguous
 // range of 64 runs of 32 positions, so L_{k-1} comes from the lane to the
 // left (or the previous run's last lane).
+constexpr uint16_t kUnset = 0xfffeu;                  // no length field takes this value
+constexpr uint32_t kUnset2 = 0xfffefffeu;
 __global__ void __launch_bounds__(kBucketThreads)
 k_bucket_llr(int32_t n, Scratch s) {
     constexpr int kChunks = kBucket / kWarp;                 // 1024 runs of 32 positions
@@ -546,15 +548,19 @@ k_bucket_llr(int32_t n, Scratch s) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) b_s = atomicAdd(&s.tickets[1], 1u);
-    for (int i = tid; i < kChunks; i += kBucketThreads) cmask[i] = 0;
+    {
+        // every length starts as kUnset: a position left unset after the
+        // scatter means sa gave another one twice
+        const uint4 u = make_uint4(kUnset2, kUnset2, kUnset2, kUnset2);
+        uint4* d = reinterpret_cast<uint4*>(sL);
+        for (int i = tid; i < kBucket / 8; i += kBucketThreads) d[i] = u;
+    }
     __syncthreads();
     const long long b = b_s;
     const long long k0 = b * kBucket;
     const int cnt = (int)(((long long)n - k0 < kBucket) ? (long long)n - k0 : kBucket);
 
-    // scatter the bucket's lengths into shared memory by position; cmask
-    // serves as a bitmap of the positions seen, so that a position given
-    // twice (sa not a permutation) is caught
+    // scatter the bucket's lengths into shared memory by position
     const uint32_t* ent = s.ent2 + ((size_t)b << kBucketLog);
     const uint32_t fill = __ldcg(s.cursor2 + (size_t)b * kCursorStride);
     unsigned bad = fill != (uint32_t)cnt;
@@ -572,16 +578,10 @@ k_bucket_llr(int32_t n, Scratch s) {
         for (int u = 0; u < kUnroll; ++u) {
             if (i0 + u * kBucketThreads + tid >= nent) continue;
             const uint32_t low = e[u] >> 17, f = e[u] & kEsc17;
-            if (low < (uint32_t)cnt) {
-                sL[low] = (uint16_t)(f == kEsc17 ? 0xffffu : f);
-                const unsigned bit = 1u << (low & 31);
-                if (atomicOr(cmask + (low >> 5), bit) & bit) bad = 1;
-            } else {
-                bad = 1;
-            }
+            if (low < (uint32_t)cnt) sL[low] = (uint16_t)(f == kEsc17 ? 0xffffu : f);
+            else bad = 1;
         }
     }
-    if (bad) report(s, kErrInput);
     __syncthreads();
     auto len_at = [&](int x) -> int32_t {                    // L of position k0 + x, 0 <= x < cnt
         const uint32_t f = sL[x];
@@ -594,10 +594,10 @@ k_bucket_llr(int32_t n, Scratch s) {
         const int x0 = warp * kRunsPerWarp * kWarp;
         left = (x0 == 0) ? ((k0 > 0) ? __ldcg(s.halo + b) : 0) : (x0 - 1 < cnt ? len_at(x0 - 1) : 0);
     }
-    __syncthreads();                                         // cmask is rewritten below
     for (int r = 0; r < kRunsPerWarp; ++r) {
         const int c = warp * kRunsPerWarp + r;
         const int x = c * kWarp + lane;
+        if (x < cnt && sL[x] == kUnset) bad = 1;
         const int32_t L = (x < cnt) ? len_at(x) : 0;
         int32_t prev = __shfl_up_sync(kFull, L, 1);
         if (lane == 0) prev = left;
@@ -605,6 +605,7 @@ k_bucket_llr(int32_t n, Scratch s) {
         const unsigned m = __ballot_sync(kFull, x < cnt && L > 0 && L >= prev);
         if (lane == 0) { cmask[c] = m; ccnt[c] = __popc(m); }
     }
+    if (bad) report(s, kErrInput);
     __syncthreads();
     // exclusive scan of the 1024 run counts: 2 per thread
     {
