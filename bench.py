@@ -546,6 +546,26 @@ def run_ours(args):
     gather_ms = g0.elapsed_time(g1) / gsteps
     per_gather = phase_avg(sa=None, rank=d_rank)
 
+    # the leftmost-only query (Algorithm 2's output, no CSR pass), same front end
+    def leftmost():
+        s_l = lr.lr_query_leftmost(ctx, d_sa, None, d_lcp, st, ln, stream)
+        if s_l != lr.LR_OK:
+            raise lr.LRError(s_l, "lr_query_leftmost")
+
+    left_ms = _event_ms(stream, leftmost, max(3, min(args.steps, 20)), warm=2)
+    lr.lr_set_phase_timing(ctx, True)
+    left_acc = None
+    for _ in range(3):
+        leftmost()
+        t = lr.lr_phase_times(ctx)
+        left_acc = list(t) if left_acc is None else [a + b for a, b in zip(left_acc, t)]
+    lr.lr_set_phase_timing(ctx, False)
+    if lr.lr_device_status(ctx, stream) != lr.LR_OK:
+        raise RuntimeError("leftmost query: device error")
+    leftmost_query = {"ms_per_step": round(left_ms, 4), "value": round(whole_job_rate(ws, n, left_ms), 3),
+                      "kernel_ms": {nm: round(a / 3, 4) for nm, a in zip(["partition", "bucket_llr", "cover"],
+                                                                         left_acc)}}
+
     # Table 2's walk statistics and the raw-LLR variant (no compaction), for comparison
     walk = lr.lr_walk_stats(ctx, d_rank, d_lcp, stream=stream)
     raw = None
@@ -692,6 +712,7 @@ def run_ours(args):
                            "definition": "LLR's covering a position, raw (alpha) and useful (beta), Table 2"},
             "raw_llr_variant": raw,
             "index_build": index_build,
+            "leftmost_query": leftmost_query,
             "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
                                   "value": round(whole_job_rate(ws, n, gather_ms), 3),
                                   "kernel_ms": {nm: round(p, 4) for nm, p in
