@@ -56,7 +56,8 @@ struct __align__(16) CoverSmem {
     int32_t spre[kChunks];           // exclusive prefix popcounts of the bitmap words
     int32_t epre[kChunks];
     int32_t chunk[kChunks];          // run totals of the tie counts
-    unsigned rt[Cfg<TP>::kWarps][6][kWarp];   // per warp: range-max levels 0..4, equal-length masks
+    unsigned rt[Cfg<TP>::kWarps][Cfg<TP>::kChunksPerWarp][kWarp];   // per warp: range-max levels 0..4 and
+                                     // equal-length masks; then the runs' tie-count prefixes
     long long tile;
     long long obase;
     int32_t lo;
@@ -311,7 +312,6 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         if (!staged) return (int32_t)p;
         return (p >> 31) ? (int32_t)((p >> 13) & 0x3ffffu) : __popc(p >> 13);
     };
-    int pre[kChunksPerWarp];
     if constexpr (kAll) {
         // CSR offsets: scan of the tie counts within the tile.  Counts are
         // almost always 0, 1 or 2: the run scan is then three ballots.  The
@@ -329,7 +329,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                        __popc(__ballot_sync(kFull, cq >= 2) & upto) +
                        __popc(__ballot_sync(kFull, cq >= 3) & upto);
             }
-            pre[q] = incl - cq;
+            RT[q][lane] = (unsigned)(incl - cq);      // exclusive prefix within the run
             if (lane == kWarp - 1) sm.chunk[q * kWarps + warp] = incl;
         }
         __syncthreads();
@@ -359,7 +359,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         for (int q = 0; q < kChunksPerWarp; ++q) {
             const int c = q * kWarps + warp;
             const int32_t k = k0 + c * kWarp + lane;
-            long long o = obase + sm.chunk[c] + pre[q];
+            long long o = obase + sm.chunk[c] + (int)RT[q][lane];
             if (k < n) __stcs(reinterpret_cast<long long*>(offsets) + k, o);
             const uint32_t p = pk[q];
             if (count_of(p) == 0) continue;
