@@ -1,6 +1,6 @@
 """The reference arm of bench.py (the CPU oracle, Algorithm 3) needs no GPU:
 its JSON line carries the same metric, unit and workload as the GPU arm,
-and the fields the driver reads."""
+and the fields a reader of the line relies on."""
 import json
 import os
 import subprocess
