@@ -187,13 +187,20 @@ def test_walk_oracles_match_brute_force():
 
 
 def test_lr_at_matches_full_run():
-    w = W.single("dna_64m", n=1 << 15)
-    full = oracle.lr_all_raw(w.rank, w.lcp)
-    ks = np.array([0, 1, 2, 100, 4095, 4096, 20000, w.n - 2, w.n - 1], np.int64)
-    ln, st, off, starts = oracle.lr_at(w.rank, w.lcp, ks)
-    for q, k in enumerate(ks):
-        assert ln[q] == full[0][k] and st[q] == full[1][k]
-        assert np.array_equal(starts[off[q]:off[q + 1]], full[3][full[2][k]:full[2][k + 1]])
+    """The per-position Algorithm 3 (used for sampled checks at full size)
+    equals the full run at every position of inputs with many ties."""
+    texts = [W.make_text("dna", 1 << 15, 6), W.iid(6000, b"ab", 8), W.iid(6000, b"abc", 9),
+             np.frombuffer(b"abcabcddbca" * 40, np.uint8)]
+    ties = 0
+    for text in texts:
+        sa, rank, lcp = W.prep(text)
+        full = oracle.lr_all_raw(rank, lcp)
+        ks = np.arange(text.size, dtype=np.int64)
+        got = oracle.lr_at(rank, lcp, ks)
+        for a, b in zip(got, full):
+            assert np.array_equal(a, b)
+        ties += int(np.sum(np.diff(full[2]) > 1))
+    assert ties > 1000
 
 
 # ---------------------------------------------------------------- invariants

@@ -42,6 +42,20 @@ MUTANTS = [
      "if (i + llrr[i] - 1 < k) { ++a; break; }\n            ++a;"),
     ("beta walk stops one early", "if (!(cs[i] <= k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;",
      "if (!(cs[i] < k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;"),
+    # the per-position Algorithm 3 used for sampled checks at full size
+    ("sampled walk break off by one",
+     "        for (int64_t i = k; i >= 0; --i) {\n            int32_t L = llr_len(rank, lcp, i);\n"
+     "            if (i + L - 1 < k) break;\n            else if (L >= length) length = L;\n        }",
+     "        for (int64_t i = k; i >= 0; --i) {\n            int32_t L = llr_len(rank, lcp, i);\n"
+     "            if (i + L < k) break;\n            else if (L >= length) length = L;\n        }"),
+    ("sampled walk keeps descending order",
+     "            for (int64_t a = first; a < hi; ++a, --hi) {\n"
+     "                int32_t t = starts[a]; starts[a] = starts[hi]; starts[hi] = t;\n            }\n        }\n"
+     "        lr_len[q] = length;",
+     "            (void)hi;\n        }\n        lr_len[q] = length;"),
+    ("sampled walk lists only the leftmost tie",
+     "                else if (L == length) {\n                    if (total < cap) starts[total] = (int32_t)i;",
+     "                else if (L == length && total == first) {\n                    if (total < cap) starts[total] = (int32_t)i;"),
 ]
 
 
@@ -71,6 +85,7 @@ def _pins_pass() -> bool:
             for st, ln in (oracle.lr_leftmost_raw(rank, lcp), oracle.lr_leftmost_compact(rank, lcp)):
                 assert np.array_equal(st, want[1]) and np.array_equal(ln, want[0])
         T.test_walk_counts_match_definition()
+        T.test_lr_at_matches_full_run()
         for n in (2, 7):
             T.test_walk_counts_closed_forms(n)
         return True
