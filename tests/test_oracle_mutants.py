@@ -42,6 +42,9 @@ MUTANTS = [
      "if (i + llrr[i] - 1 < k) { ++a; break; }\n            ++a;"),
     ("beta walk stops one early", "if (!(cs[i] <= k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;",
      "if (!(cs[i] < k && (int64_t)cs[i] + cl[i] - 1 >= k)) break;\n                ++b;"),
+    ("alg2 tie keeps the rightmost", "else if (cl[i] > best_len) { best_start = cs[i]; best_len = cl[i]; }",
+     "else if (cl[i] >= best_len) { best_start = cs[i]; best_len = cl[i]; }"),
+    ("compaction keeps empty LLR's", "if (L > 0 && L >= prev)", "if (L >= prev)"),
     # the per-position Algorithm 3 used for sampled checks at full size
     ("sampled walk break off by one",
      "        for (int64_t i = k; i >= 0; --i) {\n            int32_t L = llr_len(rank, lcp, i);\n"
