@@ -328,3 +328,26 @@ def test_prep_matches_naive_suffix_sort():
                 m += 1
             want_lcp[r] = m
         assert lcp.tolist() == want_lcp, s
+
+
+def test_prep_many_matches_per_string_prep():
+    """The batched prep (the input of every batched and serving test) is the
+    per-string prep laid out back to back: string j's local sa and rank at
+    off[j], its lcp (n_j + 1 entries) at off[j] + j; empty strings included."""
+    rng = np.random.default_rng(6)
+    lens = [0, 1, 5, 0, 300, 2, 1000, 0, 77, 3000, 1]
+    pieces = [W.make_text("dna", m, 40 + j) if m >= 64 else rng.integers(97, 100, m).astype(np.uint8)
+              for j, m in enumerate(lens)]
+    off = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=off[1:])
+    text = np.concatenate(pieces).astype(np.uint8)
+    sa, rank, lcp = W.prep_many(text, off)
+    assert sa.size == text.size and lcp.size == text.size + len(lens)
+    for j, m in enumerate(lens):
+        a = int(off[j])
+        if m == 0:
+            assert lcp[a + j] == 0
+            continue
+        s1, r1, l1 = W.prep(text[a:a + m])
+        assert np.array_equal(sa[a:a + m], s1) and np.array_equal(rank[a:a + m], r1)
+        assert np.array_equal(lcp[a + j:a + j + m + 1], l1)
