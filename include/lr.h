@@ -398,6 +398,23 @@ lr_status lr_query_all_static(lr_stream_t stream,
                               int64_t* h_total);
 
 /*
+ * Test hook for the bounded device-side waits (off by default; changes no
+ * result while off).  Every kernel that waits for another CTA's look-back
+ * status word gives up after a bounded number of polls, records a timeout
+ * and finishes, so a lost wait never hangs the GPU; this hook makes such a
+ * wait run out on purpose without any fault.  While it is on, the cover
+ * kernel's tile number `tile` (tiles of 4096 positions with the default
+ * shape) never publishes its status word, and every look-back wait of the
+ * context's queries gives up after `spin_limit` polls (1 .. 2^23; the
+ * default is 2^23).  A query whose cover has more than tile + 1 tiles then
+ * waits for a word that nothing sets, gives up, and reports LR_ERR_TIMEOUT
+ * (through h_total or lr_device_status); its outputs are invalid.  tile < 0
+ * switches the hook off and restores the default limit; the context stays
+ * usable throughout.  LR_ERR_ARG for a spin_limit out of range.
+ */
+lr_status lr_test_hold_lookback(lr_ctx* ctx, int64_t tile, int32_t spin_limit);
+
+/*
  * Kernels launched by the most recent query of this context (for the
  * benchmark's launch accounting): 4 with sa, 2 with rank only, one more for
  * a batch; 2 for the raw-LLR variant, 4 for lr_walk_stats.

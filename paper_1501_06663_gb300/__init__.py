@@ -36,6 +36,7 @@ EXPORTED = (
     "lr_server_start", "lr_server_submit", "lr_server_poll", "lr_server_wait", "lr_server_cancel",
     "lr_server_stats_get", "lr_server_stop",
     "lr_query_all_raw", "lr_query_leftmost_raw", "lr_walk_stats", "lr_build_arrays", "lr_batch_build_arrays",
+    "lr_test_hold_lookback",
 )
 
 LR_JOB_QUEUED, LR_JOB_ADMITTED, LR_JOB_RUNNING, LR_JOB_DONE, LR_JOB_CANCELLED = range(5)
@@ -114,6 +115,7 @@ def load(path: str | None = None):
     lib.lr_query_all_host.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.lr_last_launch_count.argtypes = [vp]
     lib.lr_last_launch_count.restype = i32
+    lib.lr_test_hold_lookback.argtypes = [vp, i64, i32]
     lib.lr_set_phase_timing.argtypes = [vp, i32]
     lib.lr_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
     lib.lr_phase_times.restype = i32
@@ -199,6 +201,12 @@ def lr_last_cuda_error(ctx) -> int:
 
 def lr_last_launch_count(ctx) -> int:
     return int(load().lr_last_launch_count(ctx))
+
+
+def lr_test_hold_lookback(ctx, tile: int, spin_limit: int = 1000) -> int:
+    """Test hook: cover tile `tile` keeps its look-back word unpublished and
+    waits give up after `spin_limit` polls (tile < 0: off).  Returns the status."""
+    return int(load().lr_test_hold_lookback(ctx, int(tile), int(spin_limit)))
 
 
 def lr_set_phase_timing(ctx, enable: bool) -> None:

@@ -29,6 +29,8 @@ struct lr_ctx {
     std::map<int, int> tuned;             // shape class -> shape code (lr_autotune)
     lr::IndexWork index_work;             // work memory of lr_build_arrays / lr_batch_build_arrays
     int64_t* d_off2 = nullptr;            // {0, n} for single-string builds
+    int spin_limit = lr::kSpinLimit;      // look-back poll limit of this context's queries
+    long long hold_tile = -1;             // test hook (lr_test_hold_lookback): cover tile kept unpublished
 };
 
 struct lr_plan {
@@ -138,6 +140,8 @@ lr_status get_scratch(lr_ctx* ctx, long long n, lr::Scratch* s) {
         ctx->scratch_n = n;
     }
     carve(ctx->scratch, ctx->scratch_n, n, ctx->d_err, s);
+    s->spin_limit = ctx->spin_limit;
+    s->hold_tile = ctx->hold_tile;
     ctx->last_n = n;
     return LR_OK;
 }
@@ -280,6 +284,19 @@ lr_status lr_last_cuda_error(lr_ctx* ctx, int* code) {
 }
 
 int32_t lr_last_launch_count(lr_ctx* ctx) { return ctx ? ctx->last_launches : -1; }
+
+lr_status lr_test_hold_lookback(lr_ctx* ctx, int64_t tile, int32_t spin_limit) {
+    if (!ctx) return LR_ERR_ARG;
+    if (tile < 0) {
+        ctx->hold_tile = -1;
+        ctx->spin_limit = lr::kSpinLimit;
+        return LR_OK;
+    }
+    if (spin_limit < 1 || spin_limit > lr::kSpinLimit) return LR_ERR_ARG;
+    ctx->hold_tile = tile;
+    ctx->spin_limit = spin_limit;
+    return LR_OK;
+}
 
 lr_status lr_set_phase_timing(lr_ctx* ctx, int32_t enable) {
     if (!ctx) return LR_ERR_ARG;

@@ -44,6 +44,14 @@ struct Cfg {
     static constexpr int kChunksPerWarp = kChunks / kWarps;
     static constexpr int kMinBlocks = TP == 1 ? 5 : (TP == 2 ? 4 : 2);
     static constexpr int kCap = kTileC + 128;     // staged entries: the tile's own and a carry
+    // Width of the holder-index field of the packed per-run word pk (see
+    // k_cover): every staged index v < kCap and the "none" value all-ones
+    // must fit; the holder mask or count takes the bits above it up to 30.
+    static constexpr int kVBits = (kCap <= (1 << 13) - 1) ? 13 : 14;
+    static constexpr uint32_t kNone = (1u << kVBits) - 1u;
+    static constexpr int kMaskBits = 31 - kVBits;
+    static_assert(kCap <= (int)kNone, "staged window indices must fit the holder-index field");
+    static_assert(kCap < (1 << kMaskBits), "a tie count must fit the count field");
 };
 
 template <int TP>
@@ -239,11 +247,15 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     //
     // Per run the lane keeps pk[], packed (the longest length is stored at
     // once, and read back from the leftmost holder when needed again):
-    //   staged tiles:  bits 0..12 leftmost holder v (0x1fff: none); bit 31
-    //                  clear: bits 13..30 = holders as a mask from v (bit 0 =
-    //                  v); bit 31 set: bits 13..30 = number of holders;
+    //   staged tiles:  bits 0..B-1 leftmost holder v (all ones: none), B =
+    //                  kVBits (13, or 14 for 8192-position tiles, whose
+    //                  staged indices reach 8319); bit 31 clear: bits B..30 =
+    //                  holders as a mask from v (bit 0 = v); bit 31 set:
+    //                  bits B..30 = number of holders;
     //   other tiles:   the number of holders.
-    constexpr uint32_t kNone = 0x1fffu;
+    constexpr int kVBits = Cfg<TP>::kVBits;
+    constexpr uint32_t kNone = Cfg<TP>::kNone;
+    constexpr uint32_t kFieldMask = (1u << Cfg<TP>::kMaskBits) - 1u;
     uint32_t pk[kChunksPerWarp];
     unsigned (*RT)[kWarp] = sm.rt[warp];
     // the longest length and the leftmost holder's start of a position are
@@ -292,7 +304,8 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                 const unsigned range = ((2u << h0) - 1u) & ~((1u << jl) - 1u);
                 const unsigned hold = (RT[5][jl] & range) >> jl;
                 const uint32_t v = (uint32_t)(U0 + jl);
-                p = hold < (1u << 18) ? (v | (hold << 13)) : (v | ((uint32_t)__popc(hold) << 13) | 0x80000000u);
+                p = hold <= kFieldMask ? (v | (hold << kVBits))
+                                       : (v | ((uint32_t)__popc(hold) << kVBits) | 0x80000000u);
             }
             __syncwarp();                                         // before the next run rewrites RT
             pk[q] = p;
@@ -303,14 +316,14 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             store_leftmost(c, b, vb);
             if (!staged) pk[q] = (uint32_t)ct;
             else if (ct == 0) pk[q] = kNone;
-            else if (ct == 1) pk[q] = (uint32_t)vb | (1u << 13);
-            else pk[q] = (uint32_t)vb | ((uint32_t)ct << 13) | 0x80000000u;
+            else if (ct == 1) pk[q] = (uint32_t)vb | (1u << kVBits);
+            else pk[q] = (uint32_t)vb | ((uint32_t)ct << kVBits) | 0x80000000u;
         }
     }
     // holders of run q (the tie count of its position)
     auto count_of = [&](uint32_t p) -> int32_t {
         if (!staged) return (int32_t)p;
-        return (p >> 31) ? (int32_t)((p >> 13) & 0x3ffffu) : __popc(p >> 13);
+        return (p >> 31) ? (int32_t)((p >> kVBits) & kFieldMask) : __popc(p >> kVBits);
     };
     if constexpr (kAll) {
         // CSR offsets: scan of the tie counts within the tile.  Counts are
@@ -336,7 +349,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         if (warp == 0) {
             const int tot = scan_chunks<kChunks>(sm.chunk);
             if (lane == 0) {
-                publish(s.status_o, tile, tile == 0 ? kPrefix : kAggregate, tot);
+                if (tile != s.hold_tile) publish(s.status_o, tile, tile == 0 ? kPrefix : kAggregate, tot);
                 sm.ttot = tot;
             }
         }
@@ -346,9 +359,9 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         __syncthreads();
         if (warp == 0) {
             const int tot = sm.ttot;
-            const long long ex = (tile == 0) ? 0 : lookback(s.status_o, tile, s.err, s.qerr);
+            const long long ex = (tile == 0) ? 0 : lookback(s.status_o, tile, s.err, s.qerr, s.spin_limit);
             if (lane == 0) {
-                if (tile != 0) publish(s.status_o, tile, kPrefix, ex + tot);
+                if (tile != 0 && tile != s.hold_tile) publish(s.status_o, tile, kPrefix, ex + tot);
                 sm.obase = ex;
                 if (tile == num_cover_tiles(n, TP) - 1) offsets[n] = ex + tot;
             }
@@ -367,7 +380,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             // longest length, ascending
             if (staged && !(p >> 31)) {
                 const int32_t v0 = (int32_t)(p & kNone);
-                unsigned m = p >> 13;
+                unsigned m = p >> kVBits;
                 while (m) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1u;

@@ -5,6 +5,7 @@
 // library.
 #pragma once
 #include <cstdint>
+#include "lr_internal.h"
 
 namespace lr {
 
@@ -20,10 +21,6 @@ constexpr unsigned long long kFlagShift = 62;
 constexpr unsigned long long kValMask = (1ull << kFlagShift) - 1;
 constexpr unsigned long long kAggregate = 1ull;   // value = this tile's own total
 constexpr unsigned long long kPrefix = 2ull;      // value = total of tiles 0..this one
-
-// Upper bound on polls of one status word before a wait is declared lost
-// (about a second at the back-off below).
-constexpr int kSpinLimit = 1 << 23;
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
     unsigned long long v;
@@ -57,13 +54,15 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-// Polls `w` until its flag is set; after kSpinLimit polls records a timeout
-// in both error words and returns a prefix of 0 so the caller can finish.
-__device__ __forceinline__ unsigned long long wait_flag(const unsigned long long* w, unsigned* err, unsigned* qerr) {
+// Polls `w` until its flag is set; after `limit` polls (kSpinLimit unless a
+// test shortens it) records a timeout in both error words and returns a
+// prefix of 0 so the caller can finish.
+__device__ __forceinline__ unsigned long long wait_flag(const unsigned long long* w, unsigned* err, unsigned* qerr,
+                                                        int limit) {
     unsigned long long v = ld_acquire(w);
     int polls = 0;
     while ((v >> kFlagShift) == 0) {
-        if (++polls >= kSpinLimit) {
+        if (++polls >= limit) {
             atomicOr(err, kErrTimeout);
             atomicOr(qerr, kErrTimeout);
             return kPrefix << kFlagShift;
@@ -85,13 +84,13 @@ __device__ __forceinline__ void publish(unsigned long long* status, long long ti
 // publish the inclusive prefix.  Waits only on earlier tiles, which were
 // scheduled before this one.
 __device__ __forceinline__ long long lookback(const unsigned long long* status, long long tile, unsigned* err,
-                                              unsigned* qerr) {
+                                              unsigned* qerr, int limit) {
     const unsigned lane = lane_id();
     long long exclusive = 0;
     long long base = tile - 1;
     while (base >= 0) {
         const long long t = base - (long long)lane;
-        const unsigned long long w = (t >= 0) ? wait_flag(&status[t], err, qerr) : (kPrefix << kFlagShift);
+        const unsigned long long w = (t >= 0) ? wait_flag(&status[t], err, qerr, limit) : (kPrefix << kFlagShift);
         const unsigned pmask = __ballot_sync(kFull, (w >> kFlagShift) == kPrefix);
         const int stop = pmask ? __ffs(pmask) - 1 : kWarp - 1;
         const long long contrib = ((int)lane <= stop) ? (long long)(w & kValMask) : 0;
@@ -104,11 +103,12 @@ __device__ __forceinline__ long long lookback(const unsigned long long* status, 
 
 // Publish-aggregate, look back, publish-prefix in one call (one whole warp).
 __device__ __forceinline__ long long lookback_exclusive(unsigned long long* status, long long tile,
-                                                       long long aggregate, unsigned* err, unsigned* qerr) {
+                                                       long long aggregate, unsigned* err, unsigned* qerr,
+                                                       int limit) {
     const unsigned lane = lane_id();
     if (lane == 0) publish(status, tile, tile == 0 ? kPrefix : kAggregate, aggregate);
     if (tile == 0) return 0;
-    const long long ex = lookback(status, tile, err, qerr);
+    const long long ex = lookback(status, tile, err, qerr, limit);
     if (lane == 0) publish(status, tile, kPrefix, ex + aggregate);
     return ex;
 }

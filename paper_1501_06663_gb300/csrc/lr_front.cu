@@ -233,7 +233,7 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
     }
     // K3: the tile's place in LLRc.
     if (warp == 0) {
-        const long long ex = lookback_exclusive(s.status_g, tile, total_s, s.err, s.qerr);
+        const long long ex = lookback_exclusive(s.status_g, tile, total_s, s.err, s.qerr, s.spin_limit);
         if (lane == 0) {
             base_s = ex;
             s.tile_cbase[tile] = (int32_t)ex;
@@ -626,7 +626,7 @@ k_bucket_llr(int32_t n, Scratch s) {
     }
     __syncthreads();
     if (warp == 0) {
-        const long long ex = lookback_exclusive(s.status_b, b, total_s, s.err, s.qerr);
+        const long long ex = lookback_exclusive(s.status_b, b, total_s, s.err, s.qerr, s.spin_limit);
         if (lane == 0) base_s = ex;
     }
     __syncthreads();

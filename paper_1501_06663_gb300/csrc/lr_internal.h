@@ -13,7 +13,7 @@ constexpr int kThreads = 256;        // threads per tile CTA
 // Tiles of the cover kernel: kTile x (1 or 2) positions, kThreads x the same threads.
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
-// position, into super-buckets of 2^20 and then buckets of 2^16 positions.
+// position, into super-buckets of 2^20 and then buckets of 2^15 positions.
 constexpr int kSuperLog = 20;
 constexpr int kSuper = 1 << kSuperLog;         // positions per super-bucket
 constexpr int kBucketLog = 15;
@@ -27,6 +27,10 @@ constexpr int kPartRound = kPartThreads * kPartPer;   // 4096 entries per partit
 constexpr uint32_t kEsc12 = 0xfffu;            // 12-bit length field of level 1: value in lbig
 constexpr uint32_t kEsc17 = 0x1ffffu;          // 17-bit length field of level 2: value in lbig
 constexpr int kCursorStride = 32;              // one 128-byte line per partition cursor
+
+// Polls of a look-back status word before the wait is declared lost (a
+// few seconds at most; the kernel then reports kErrTimeout and finishes).
+constexpr int kSpinLimit = 1 << 23;
 
 // Device scratch of one query, carved out of one allocation by the context.
 struct Scratch {
@@ -51,6 +55,8 @@ struct Scratch {
     long long nsupers;
     void* zero_base;               // tickets, status words and cursors, cleared before every query
     size_t zero_bytes;
+    int spin_limit = kSpinLimit;   // polls of one look-back wait before it gives up
+    long long hold_tile = -1;      // test hook: this cover tile never publishes its look-back word
 };
 
 __host__ __device__ inline long long num_tiles(long long n) { return (n + kTile - 1) / kTile; }

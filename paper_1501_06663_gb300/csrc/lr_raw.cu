@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kRawThreads) k_rawwalk(int32_t n, const int32_
         __syncthreads();
         if (warp == 0) {
             const int tot = scan_runs(run_tot);
-            const long long ex = lookback_exclusive(s.status_o, tile, tot, s.err, s.qerr);
+            const long long ex = lookback_exclusive(s.status_o, tile, tot, s.err, s.qerr, s.spin_limit);
             if (lane == 0) {
                 obase_s = ex;
                 if (k0 + kRawTile >= n) offsets[n] = ex + tot;

@@ -23,9 +23,7 @@ constexpr size_t kZeroEnd = kOffStatusO + (size_t)kTilesMax * 8;
 constexpr size_t kOffCbase = align_s(kZeroEnd);
 constexpr size_t kOffCstart = align_s(kOffCbase + (size_t)(kTilesMax + 1) * 4);
 constexpr size_t kOffCend = align_s(kOffCstart + (size_t)kStaticMaxN * 4);
-// (the cover kernel's 16-byte-wide bulk copies may read up to 3 entries past
-// the ends array: one slack block)
-constexpr size_t kStaticBytes = align_s(kOffCend + (size_t)kStaticMaxN * 4) + kAlignS;   // about 8.1 MB
+constexpr size_t kStaticBytes = align_s(kOffCend + (size_t)kStaticMaxN * 4);   // about 8.1 MB
 
 // The array itself.  Host code must not use its name as an address: it is a
 // host-side stand-in.  The device address comes from cudaGetSymbolAddress.

@@ -266,3 +266,47 @@ def test_every_shape_code_matches_the_oracle(ctx, code, tmp_path):
         _assert_equal(got, _expected(off, rank_b, lcp_b), "batch, code %d" % code)
     finally:
         c.close()
+
+
+def _dense_compact_text(seed, front, w=40):
+    """A random ACGT string R of 3 x 8192 + 200 symbols, then every length-w
+    window of R followed by '#', with `front` random bytes before R.  Every
+    position of R (but its last w) has L = w (the window copy repeats it and
+    the '#' ends the repeat), so it is a compact LLR: whole 8192-position
+    cover tiles consist of compact LLR's, plus w - 1 carried from the tile
+    before, and the staged window indices run past 8191."""
+    rng = np.random.default_rng(seed)
+    R = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 3 * 8192 + 200)]
+    win = np.lib.stride_tricks.sliding_window_view(R, w)
+    tail = np.concatenate([win, np.full((win.shape[0], 1), ord("#"), np.uint8)], axis=1).reshape(-1)
+    head = rng.integers(0, 256, front).astype(np.uint8)
+    return np.concatenate([head, R, tail])
+
+
+@pytest.mark.parametrize("code", [0, 1, 4, 2, 3, 6])
+def test_every_shape_code_on_tiles_of_compact_llrs(ctx, code, tmp_path):
+    """Each shape code on an input whose cover tiles consist entirely of
+    compact LLR's (the packed holder index of a staged 8192-position tile
+    then needs 14 bits), with the tile grid at two offsets into the dense
+    region; single string and batch (the dense string between two others)."""
+    lg = lambda v: int(v).bit_length() - 1
+    c = P.Context(0)
+    try:
+        for front in (0, 100):
+            text = _dense_compact_text(21, front)
+            sa, rank, lcp = W.prep(text)
+            rng = np.random.default_rng(5 + front)
+            btext = np.concatenate([_random_text(rng, 300, 4), text, _random_text(rng, 5000, 3)])
+            off = _offsets([300, text.size, 5000])
+            sa_b, rank_b, lcp_b = _batch(btext, off)
+            classes = [lg(text.size) * 64 + lg(text.size), lg(off[-1]) * 64 + lg(int(off[-1]) // 3)]
+            path = tmp_path / ("codes%d.txt" % front)
+            path.write_text("".join("%d %d\n" % (cl, code) for cl in classes))
+            P.lr_autotune_load(c.handle, str(path))
+            got = tuple(t.cpu().numpy() for t in c.query_all(_dev(lcp), sa=_dev(sa), rank=_dev(rank)))
+            _assert_equal(got, oracle.lr_all_raw(rank, lcp), "single, code %d, front %d" % (code, front))
+            got = tuple(t.cpu().numpy() for t in
+                        c.query_batch(_dev(off), _dev(lcp_b), sa=_dev(sa_b), rank=_dev(rank_b)))
+            _assert_equal(got, _expected(off, rank_b, lcp_b), "batch, code %d, front %d" % (code, front))
+    finally:
+        c.close()
