@@ -234,16 +234,19 @@ lr_status lr_batch_query_all(lr_ctx* ctx, lr_stream_t stream, const lr_batch_des
                              int64_t* h_total);
 
 /*
- * Autotuning.  Kernel shape choices (the cover tile: 2048, 4096 or 8192
- * positions; the front end, when both sa and rank are given) are timed on
- * the given batch (a single string is a batch with num = 1) and the fastest
- * is remembered in the context for batches of the same shape class (total
- * size and mean string length, both rounded to powers of two).  Later
- * queries of that class use it.  *choice receives the chosen shape code
- * (bit 0: 4096-position cover tile, bit 2: 8192-position cover tile, neither:
- * 2048; bit 1: rank-gather front end).  The
- * outputs are overwritten.  lr_autotune_save / _load write and read the
- * remembered choices as a small text file (one "class code" pair per line).
+ * Autotuning.  Kernel shape choices (the cover kernel: warp segments of 256
+ * positions, or CTA tiles of 2048, 4096 or 8192 positions; the front end,
+ * when both sa and rank are given) are timed on the given batch (a single
+ * string is a batch with num = 1) and the fastest is remembered in the
+ * context for batches of the same shape class (total size and mean string
+ * length, both rounded to powers of two).  Later queries of that class use
+ * it; the default is the tile cover with 4096-position tiles and the
+ * rank-order front end (code 9).  *choice receives the chosen shape code: bit 3 clear: the
+ * warp-segment cover (bits 0 and 2 clear); bit 3 set: the tile cover, with
+ * bit 0: 4096-position tiles, bit 2: 8192-position tiles, neither: 2048;
+ * bit 1: the rank-gather front end.  The outputs are overwritten.
+ * lr_autotune_save / _load write and read the remembered choices as a small
+ * text file (one "class code" pair per line; invalid codes are skipped).
  */
 lr_status lr_autotune(lr_ctx* ctx, lr_stream_t stream, const lr_batch_desc* batch,
                       int32_t* d_lr_len, int32_t* d_lr_start, int64_t* d_offsets, int32_t* d_starts,
@@ -403,11 +406,12 @@ lr_status lr_query_all_static(lr_stream_t stream,
  * status word gives up after a bounded number of polls, records a timeout
  * and finishes, so a lost wait never hangs the GPU; this hook makes such a
  * wait run out on purpose without any fault.  While it is on, the cover
- * kernel's tile number `tile` (tiles of 4096 positions with the default
- * shape) never publishes its status word, and every look-back wait of the
- * context's queries gives up after `spin_limit` polls (1 .. 2^23; the
- * default is 2^23).  A query whose cover has more than tile + 1 tiles then
- * waits for a word that nothing sets, gives up, and reports LR_ERR_TIMEOUT
+ * kernel's look-back unit number `tile` (a tile of 4096 positions with the
+ * default warp-segment cover or with the tile cover's default shape) never
+ * publishes its status word, and every look-back wait of the context's
+ * queries gives up after `spin_limit` polls (1 .. 2^23; the default is
+ * 2^23).  A query whose cover has more than tile + 1 units then waits for a
+ * word that nothing sets, gives up, and reports LR_ERR_TIMEOUT
  * (through h_total or lr_device_status); its outputs are invalid.  tile < 0
  * switches the hook off and restores the default limit; the context stays
  * usable throughout.  LR_ERR_ARG for a spin_limit out of range.

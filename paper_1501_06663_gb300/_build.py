@@ -12,7 +12,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build_obj")
 LIB_PATH = os.path.join(PKG, "liblr.so")
 
-SOURCES = ["lr_front.cu", "lr_cover.cu", "lr_query.cu", "lr_api.cu", "lr_static.cu", "lr_server.cu", "lr_raw.cu", "lr_index.cu"]
+SOURCES = ["lr_front.cu", "lr_cover.cu", "lr_cover_w.cu", "lr_query.cu", "lr_api.cu", "lr_static.cu", "lr_server.cu", "lr_raw.cu", "lr_index.cu"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -70,21 +70,24 @@ lr_status cuda_fail(lr_ctx* ctx, cudaError_t e) {
 }
 
 struct Layout {
-    size_t off_status_g, off_status_b, off_status_o, off_cursor1, off_cursor2, zero_end;
-    size_t off_tile_cbase, off_tile_seg, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo, total;
+    size_t off_status_g, off_status_b, off_status_o, off_status_w, off_cursor1, off_cursor2, zero_end;
+    size_t off_tile_cbase, off_seg_cbase, off_tile_seg, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo,
+        total;
 };
 
 Layout layout_for(long long n) {
-    const long long nt = lr::num_tiles(n), nb = lr::num_buckets(n), ns = lr::num_supers(n);
+    const long long nt = lr::num_tiles(n), nb = lr::num_buckets(n), ns = lr::num_supers(n), ng = lr::num_segs(n);
     Layout L;
     L.off_status_g = kAlign;                       // tickets in [0, 16), per-query error bits at 16
     L.off_status_b = align_up(L.off_status_g + (size_t)nt * 8);
     L.off_status_o = align_up(L.off_status_b + (size_t)nb * 8);
-    L.off_cursor1 = align_up(L.off_status_o + (size_t)nt * 8);
+    L.off_status_w = align_up(L.off_status_o + (size_t)nt * 8);
+    L.off_cursor1 = align_up(L.off_status_w + (size_t)ng * 8);
     L.off_cursor2 = align_up(L.off_cursor1 + (size_t)ns * 4 * lr::kCursorStride);
     L.zero_end = L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride;
     L.off_tile_cbase = align_up(L.zero_end);
-    L.off_tile_seg = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
+    L.off_seg_cbase = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
+    L.off_tile_seg = align_up(L.off_seg_cbase + (size_t)(ng + 1) * 4);
     L.off_cstart = align_up(L.off_tile_seg + (size_t)nt * 4);
     L.off_cend = align_up(L.off_cstart + (size_t)n * 4);
     L.off_ent1 = align_up(L.off_cend + (size_t)n * 4);
@@ -105,6 +108,8 @@ void carve(unsigned char* b, long long cap_n, long long n, unsigned* d_err, lr::
     s->status_g = (unsigned long long*)(b + L.off_status_g);
     s->status_b = (unsigned long long*)(b + L.off_status_b);
     s->status_o = (unsigned long long*)(b + L.off_status_o);
+    s->status_w = (unsigned long long*)(b + L.off_status_w);
+    s->seg_cbase = (int32_t*)(b + L.off_seg_cbase);
     s->cursor1 = (unsigned*)(b + L.off_cursor1);
     s->cursor2 = (unsigned*)(b + L.off_cursor2);
     s->tile_cbase = (int32_t*)(b + L.off_tile_cbase);
@@ -116,6 +121,7 @@ void carve(unsigned char* b, long long cap_n, long long n, unsigned* d_err, lr::
     s->lbig = (int32_t*)(b + L.off_lbig);
     s->halo = (int32_t*)(b + L.off_halo);
     s->ntiles = lr::num_tiles(n);
+    s->nsegs = lr::num_segs(n);
     s->nbuckets = lr::num_buckets(n);
     s->nsupers = lr::num_supers(n);
     s->zero_base = b;
@@ -169,19 +175,27 @@ int shape_class(long long total, long long num) {
 
 lr::Shape shape_of(int code) {
     lr::Shape sh;
+    sh.tile_cover = (code & 8) != 0;
     sh.cover_tiles_per = (code & 4) ? 4 : ((code & 1) ? 2 : 1);
     return sh;
 }
 
-// Shape codes lr_autotune tries: cover tiles of 2048, 4096 or 8192
-// positions (bit 0 / bit 2), each with either front end (bit 1).
-constexpr int kShapeCodes[] = {0, 1, 4, 2, 3, 6};
+// Shape codes lr_autotune tries: the warp-segment cover (bit 3 clear) or the
+// tile cover (bit 3) with tiles of 2048, 4096 or 8192 positions (bit 0 /
+// bit 2), each with either front end (bit 1).
+constexpr int kShapeCodes[] = {0, 2, 8, 9, 12, 10, 11, 14};
 
-// The tuned shape code for a batch (default: 4096-position cover tiles,
-// rank-order front end).
+bool valid_code(int code) {
+    if (code < 0 || code >= 16) return false;
+    return (code & 8) ? (code & 5) != 5 : (code & 5) == 0;
+}
+
+// The tuned shape code for a batch (default: tile cover with 4096-position
+// tiles, rank-order front end).
+constexpr int kDefaultCode = 9;
 int tuned_code(const lr_ctx* ctx, long long total, long long num) {
     auto it = ctx->tuned.find(shape_class(total, num));
-    return it == ctx->tuned.end() ? 1 : it->second;
+    return it == ctx->tuned.end() ? kDefaultCode : it->second;
 }
 
 lr_status check_n(int32_t n) {
@@ -676,7 +690,7 @@ lr_status lr_autotune_load(lr_ctx* ctx, const char* path) {
     if (!f) return LR_ERR_ARG;
     int cls = 0, code = 0;
     while (std::fscanf(f, "%d %d", &cls, &code) == 2)
-        if (code >= 0 && code < 8 && (code & 5) != 5) ctx->tuned[cls] = code;
+        if (valid_code(code)) ctx->tuned[cls] = code;
     std::fclose(f);
     return LR_OK;
 }

@@ -71,6 +71,7 @@ struct __align__(16) CoverSmem {
     int32_t lo;
     int32_t nlow;                    // staged carry candidates that end before the tile
     int32_t ttot;                    // the tile's total of tie counts
+    int32_t longlen;                 // a staged length reaches 2^27 (too long for the range-max keys)
 };
 
 // Exclusive prefix popcounts of the kChunks bitmap words, by one warp.
@@ -118,7 +119,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) sm.tile = atomicAdd(&s.tickets[2], 1u);
     if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
-    if (tid == 0) sm.nlow = 0;
+    if (tid == 0) { sm.nlow = 0; sm.longlen = 0; }
     __syncthreads();
     const long long tile = sm.tile;
     const int32_t k0 = (int32_t)(tile * kCoverTile);         // n < 2^31: positions fit 32 bits
@@ -151,6 +152,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                 const int32_t cs = __ldg(s.cstart + sbase + i), ce = __ldg(s.cend + sbase + i);
                 sm.cs[i] = cs;
                 sm.cl[i] = ce - cs + 1;
+                if (ce - cs + 1 >= (1 << 27)) sm.longlen = 1;
                 const uint32_t xs = (uint32_t)(cs - k0), xe = (uint32_t)(ce - k0);
                 if (i >= nspec && xs < (uint32_t)kCoverTile) atomicOr(&sm.smap[xs >> 5], 1u << (xs & 31));
                 if (xe < (uint32_t)kCoverTile) atomicOr(&sm.emap[xe >> 5], 1u << (xe & 31));
@@ -164,7 +166,7 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     // staged unless every staged candidate reaches k0 with more LLRc before
     // them: then the carry may be longer, and it is found in LLRc itself
     const int32_t nlow = sm.nlow;
-    const bool staged = fits && !(sbase > 0 && nlow == 0);
+    const bool staged = fits && !(sbase > 0 && nlow == 0) && !sm.longlen;
     int32_t lo = sbase + nlow;
     if (!staged) {
         if (tid < kChunks) { sm.smap[tid] = 0; sm.emap[tid] = 0; }
@@ -274,16 +276,12 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
         window(c, lw, hi);
         const int32_t U0 = __shfl_sync(kFull, lw, 0);
         const int32_t usz = __shfl_sync(kFull, hi, kWarp - 1) - U0 + 1;
-        bool fast = staged && usz <= kWarp;                       // warp-uniform
-        int32_t len_l = 0;
+        const bool fast = staged && usz <= kWarp;                 // warp-uniform; staged lengths < 2^27
         if (fast) {
-            len_l = ((int)lane < usz) ? SCL[U0 + (int)lane] : 0;
-            fast = !__any_sync(kFull, len_l >= (1 << 27));       // keys need length < 2^27
-        }
-        if (fast) {
+            const int32_t len_l = ((int)lane < usz) ? SCL[U0 + (int)lane] : 0;
             unsigned key = ((int)lane < usz) ? (((unsigned)len_l << 5) | (31u - lane)) : 0u;
             RT[0][lane] = key;
-            RT[5][lane] = __match_any_sync(kFull, len_l);
+            if constexpr (kAll) RT[5][lane] = __match_any_sync(kFull, len_l);
 #pragma unroll
             for (int l = 1; l <= 4; ++l) {
                 const unsigned o = __shfl_down_sync(kFull, key, 1u << (l - 1));
@@ -291,25 +289,33 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
                 RT[l][lane] = key;
             }
             __syncwarp();
-            int32_t b = 0;
+            // every lane queries (an empty window reads a harmless entry and
+            // is then discarded), so the warp does not diverge
+            const bool valid = lw <= hi;
+            const int l0 = valid ? lw - U0 : 0, h0 = valid ? hi - U0 : 0;
+            int lv = 31 - __clz(h0 - l0 + 1);
+            lv = lv > 4 ? 4 : lv;
+            const unsigned ka = RT[lv][l0], kb = RT[lv][h0 - (1 << lv) + 1];
+            const unsigned kk = ka > kb ? ka : kb;
+            const int jl = 31 - (int)(kk & 31u);
+            const int32_t b = valid ? (int32_t)(kk >> 5) : 0;
+            const int32_t sj = SCS[valid ? U0 + jl : 0];
             uint32_t p = kNone;
-            if (lw <= hi) {
-                const int l0 = lw - U0, h0 = hi - U0;
-                int lv = 31 - __clz(h0 - l0 + 1);
-                lv = lv > 4 ? 4 : lv;
-                const unsigned ka = RT[lv][l0], kb = RT[lv][h0 - (1 << lv) + 1];
-                const unsigned kk = ka > kb ? ka : kb;
-                b = (int32_t)(kk >> 5);
-                const int jl = 31 - (int)(kk & 31u);
+            if constexpr (kAll) {
                 const unsigned range = ((2u << h0) - 1u) & ~((1u << jl) - 1u);
                 const unsigned hold = (RT[5][jl] & range) >> jl;
                 const uint32_t v = (uint32_t)(U0 + jl);
-                p = hold <= kFieldMask ? (v | (hold << kVBits))
-                                       : (v | ((uint32_t)__popc(hold) << kVBits) | 0x80000000u);
+                const uint32_t pm = hold <= kFieldMask ? (v | (hold << kVBits))
+                                                       : (v | ((uint32_t)__popc(hold) << kVBits) | 0x80000000u);
+                p = valid ? pm : kNone;
             }
             __syncwarp();                                         // before the next run rewrites RT
             pk[q] = p;
-            store_leftmost(c, b, (int32_t)(p & kNone));
+            const int32_t k = k0 + c * kWarp + lane;
+            if (k < n) {
+                __stcs(lr_len + k, b);
+                __stcs(lr_start + k, valid ? sj : -1);
+            }
         } else {
             int32_t b, vb, ct;
             best_of(lw, hi, b, vb, ct);
@@ -327,23 +333,26 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
     };
     if constexpr (kAll) {
         // CSR offsets: scan of the tie counts within the tile.  Counts are
-        // almost always 0, 1 or 2: the run scan is then three ballots.  The
-        // tile's total is published before the per-position stores, so that
-        // later tiles rarely wait for it.
+        // almost always below 4: the run scan is then two ballots (the
+        // counts' bit planes).  The tile's total is published before the
+        // per-position stores of pass 2, so that later tiles rarely wait for
+        // it.
 #pragma unroll
         for (int q = 0; q < kChunksPerWarp; ++q) {
             const int32_t cq = count_of(pk[q]);
-            int incl;
-            if (__any_sync(kFull, cq > 3)) {
-                incl = warp_incl_scan(cq);
+            int ex, tot;
+            const unsigned big = __ballot_sync(kFull, cq > 3);
+            if (big == 0u) {                              // two bit planes of counts below 4
+                const unsigned b0 = __ballot_sync(kFull, cq & 1), b1 = __ballot_sync(kFull, cq & 2);
+                ex = __popc(b0 & below) + 2 * __popc(b1 & below);
+                tot = __popc(b0) + 2 * __popc(b1);
             } else {
-                const unsigned upto = below | (1u << lane);
-                incl = __popc(__ballot_sync(kFull, cq >= 1) & upto) +
-                       __popc(__ballot_sync(kFull, cq >= 2) & upto) +
-                       __popc(__ballot_sync(kFull, cq >= 3) & upto);
+                const int incl = warp_incl_scan(cq);
+                ex = incl - cq;
+                tot = __shfl_sync(kFull, incl, kWarp - 1);
             }
-            RT[q][lane] = (unsigned)(incl - cq);      // exclusive prefix within the run
-            if (lane == kWarp - 1) sm.chunk[q * kWarps + warp] = incl;
+            RT[q][lane] = (unsigned)ex;               // exclusive prefix within the run
+            if (lane == 0) sm.chunk[q * kWarps + warp] = tot;
         }
         __syncthreads();
         if (warp == 0) {
@@ -375,7 +384,8 @@ k_cover(int32_t n, Scratch s, int32_t* __restrict__ lr_len, int32_t* __restrict_
             long long o = obase + sm.chunk[c] + (int)RT[q][lane];
             if (k < n) __stcs(reinterpret_cast<long long*>(offsets) + k, o);
             const uint32_t p = pk[q];
-            if (count_of(p) == 0) continue;
+            const int32_t cq = count_of(p);
+            if (cq == 0) continue;
             // the second walk of Algorithm 4: every compact LLR of the
             // longest length, ascending
             if (staged && !(p >> 31)) {

@@ -1,5 +1,5 @@
-// Device helpers shared by the longest-repeat kernels: acquire/release
-// accesses of tile status words and the warp-cooperative decoupled look-back
+// Device helpers shared by the longest-repeat kernels: accesses of tile
+// status words and the warp-cooperative decoupled look-back
 // of a single-pass prefix scan (Merrill and Garland, "Single-pass Parallel
 // Prefix Scan with Decoupled Look-back", NVIDIA TR 2016), written for this
 // library.
@@ -22,14 +22,13 @@ constexpr unsigned long long kValMask = (1ull << kFlagShift) - 1;
 constexpr unsigned long long kAggregate = 1ull;   // value = this tile's own total
 constexpr unsigned long long kPrefix = 2ull;      // value = total of tiles 0..this one
 
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+// A status word carries its own value and guards no other data (readers
+// use only the flag and the count in it), so relaxed gpu-scope accesses
+// suffice: no fence makes a publishing thread wait for its earlier stores.
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
@@ -54,45 +53,47 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
     return v;
 }
 
-// Polls `w` until its flag is set; after `limit` polls (kSpinLimit unless a
-// test shortens it) records a timeout in both error words and returns a
-// prefix of 0 so the caller can finish.
-__device__ __forceinline__ unsigned long long wait_flag(const unsigned long long* w, unsigned* err, unsigned* qerr,
-                                                        int limit) {
-    unsigned long long v = ld_acquire(w);
-    int polls = 0;
-    while ((v >> kFlagShift) == 0) {
-        if (++polls >= limit) {
-            atomicOr(err, kErrTimeout);
-            atomicOr(qerr, kErrTimeout);
-            return kPrefix << kFlagShift;
-        }
-        __nanosleep(32);
-        v = ld_acquire(w);
-    }
-    return v;
-}
-
 __device__ __forceinline__ void publish(unsigned long long* status, long long tile, unsigned long long flag,
                                         long long value) {
-    st_release(&status[tile], (flag << kFlagShift) | (unsigned long long)value);
+    st_relaxed(&status[tile], (flag << kFlagShift) | (unsigned long long)value);
 }
 
 // Called by one whole warp after the tile published its aggregate.  Sums the
 // totals of all earlier tiles by looking back over their status words and
 // returns that exclusive prefix (the same value in every lane); it does not
-// publish the inclusive prefix.  Waits only on earlier tiles, which were
-// scheduled before this one.
+// publish the inclusive prefix.  Lane j reads tile base - j; only the tiles
+// after the nearest one holding an inclusive prefix (and that one) are
+// needed, so only their lanes wait for a word still unset.  Waits only on
+// earlier tiles, which were scheduled before this one; after `limit` polls
+// (kSpinLimit unless a test shortens it) a missing word counts as a prefix
+// of 0 and a timeout is recorded in both error words.
 __device__ __forceinline__ long long lookback(const unsigned long long* status, long long tile, unsigned* err,
                                               unsigned* qerr, int limit) {
     const unsigned lane = lane_id();
     long long exclusive = 0;
     long long base = tile - 1;
+    int polls = 0;
     while (base >= 0) {
         const long long t = base - (long long)lane;
-        const unsigned long long w = (t >= 0) ? wait_flag(&status[t], err, qerr, limit) : (kPrefix << kFlagShift);
-        const unsigned pmask = __ballot_sync(kFull, (w >> kFlagShift) == kPrefix);
-        const int stop = pmask ? __ffs(pmask) - 1 : kWarp - 1;
+        unsigned long long w = (t >= 0) ? ld_relaxed(&status[t]) : (kPrefix << kFlagShift);
+        unsigned pmask;
+        int stop;
+        for (;;) {
+            pmask = __ballot_sync(kFull, (w >> kFlagShift) == kPrefix);
+            stop = pmask ? __ffs(pmask) - 1 : kWarp - 1;
+            const bool missing = (int)lane <= stop && (w >> kFlagShift) == 0;
+            if (!__any_sync(kFull, missing)) break;
+            if (++polls >= limit) {
+                if (lane == 0) {
+                    atomicOr(err, kErrTimeout);
+                    atomicOr(qerr, kErrTimeout);
+                }
+                if (missing) w = kPrefix << kFlagShift;
+                continue;
+            }
+            __nanosleep(64);
+            if (missing) w = ld_relaxed(&status[t]);
+        }
         const long long contrib = ((int)lane <= stop) ? (long long)(w & kValMask) : 0;
         exclusive += warp_sum_ll(contrib);
         if (pmask) break;

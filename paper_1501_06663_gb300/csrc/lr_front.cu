@@ -3,8 +3,9 @@
 // 1501.06663): every position i with L_i > 0 and L_i >= L_{i-1}, in
 // ascending i, as cstart[t] = i, cend[t] = i + L_i - 1, where
 // L_i = max(lcp[rank[i]], lcp[rank[i]+1]) (Lemma 1).  They also record, for
-// every tile of kTile positions, the index of its first LLRc entry
-// (tile_cbase), which the cover kernel starts from.
+// every tile of kTile positions and every segment of kSeg positions, the
+// index of its first LLRc entry (tile_cbase, seg_cbase), which the cover
+// kernels start from.
 //
 // Two front ends compute the same LLRc:
 //
@@ -243,6 +244,12 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
     __syncthreads();
     const long long base = base_s;
     const int total = total_s;
+    // first LLRc entry of each kSeg-position segment of the tile
+    if (tid < kTile / kSeg) {
+        const long long sg = tile * (kTile / kSeg) + tid;
+        if (sg < s.nsegs) s.seg_cbase[sg] = (int32_t)(base + chunk[tid * (kSeg / kWarp)]);
+        if (sg == s.nsegs - 1) s.seg_cbase[s.nsegs] = (int32_t)(base + total);
+    }
     for (int i = tid; i < total; i += kThreads) {
         s.cstart[base + i] = c_s[i];
         s.cend[base + i] = c_e[i];
@@ -631,11 +638,16 @@ k_bucket_llr(int32_t n, Scratch s) {
     }
     __syncthreads();
     const long long base = base_s;
-    // first LLRc entry of each tile of the bucket
+    // first LLRc entry of each tile and of each kSeg-position segment of the bucket
     if (tid < kTilesPerBucket) {
         const long long tile = b * kTilesPerBucket + tid;
         if (tile < s.ntiles) s.tile_cbase[tile] = (int32_t)(base + ccnt[tid * (kTile / kWarp)]);
         if (tile == s.ntiles - 1) s.tile_cbase[s.ntiles] = (int32_t)(base + total_s);
+    }
+    for (int j = tid; j < kBucket / kSeg; j += kBucketThreads) {
+        const long long sg = b * (kBucket / kSeg) + j;
+        if (sg < s.nsegs) s.seg_cbase[sg] = (int32_t)(base + ccnt[j * (kSeg / kWarp)]);
+        if (sg == s.nsegs - 1) s.seg_cbase[s.nsegs] = (int32_t)(base + total_s);
     }
     // K3: write the kept LLR's
     for (int r = 0; r < kRunsPerWarp; ++r) {

@@ -10,7 +10,11 @@ namespace lr {
 // Tiles of the gather front end (and the granularity of tile_cbase).
 constexpr int kTile = 2048;          // positions per tile (one CTA)
 constexpr int kThreads = 256;        // threads per tile CTA
-// Tiles of the cover kernel: kTile x (1 or 2) positions, kThreads x the same threads.
+// Tiles of the tile cover kernel: kTile x (1, 2 or 4) positions, kThreads x the same threads.
+// Segments of the warp-segment cover kernel (one warp each), and the
+// granularity of seg_cbase.
+constexpr int kSegLog = 8;
+constexpr int kSeg = 1 << kSegLog;   // positions per warp segment
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
 // position, into super-buckets of 2^20 and then buckets of 2^15 positions.
@@ -50,7 +54,10 @@ struct Scratch {
     int32_t* lbig;                 // n: L of positions whose length field escaped
     int32_t* halo;                 // nbuckets + 1: L of the position before each bucket
     int32_t* tile_seg;             // ntiles: first string overlapping each tile (batched queries)
+    int32_t* seg_cbase;            // nsegs + 1: compact LLR's starting before segment j (kSeg positions)
+    unsigned long long* status_w;  // look-back words of the warp-segment cover kernel (per segment)
     long long ntiles;
+    long long nsegs;
     long long nbuckets;
     long long nsupers;
     void* zero_base;               // tickets, status words and cursors, cleared before every query
@@ -63,6 +70,7 @@ __host__ __device__ inline long long num_tiles(long long n) { return (n + kTile 
 __host__ __device__ inline long long num_cover_tiles(long long n, int tiles_per) {
     return (n + (long long)kTile * tiles_per - 1) / ((long long)kTile * tiles_per);
 }
+__host__ __device__ inline long long num_segs(long long n) { return (n + kSeg - 1) / kSeg; }
 inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
 inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
 
@@ -87,7 +95,8 @@ constexpr int kSegCap = 1024;      // strings per CTA a front end keeps in share
 
 // Kernel shape choices a query can take (picked by lr_autotune_*).
 struct Shape {
-    int cover_tiles_per = 2;       // cover tile = kTile x this (1, 2 or 4)
+    bool tile_cover = true;        // the tile cover kernel (else the warp-segment one)
+    int cover_tiles_per = 2;       // its tile = kTile x this (1, 2 or 4)
 };
 
 // Launches the whole query on `stream`: the front end (rank-order when sa is
@@ -106,6 +115,8 @@ void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Sc
 void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream);
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
                   int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream);
+void launch_cover_w(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
+                    int32_t* starts, long long capacity, bool all, cudaStream_t stream);
 
 cudaError_t configure_kernels();
 

@@ -1,6 +1,7 @@
 // Launch sequence of one longest-repeat query on a stream: clear the
 // per-query status words, run a front end (lr_front.cu) that builds the
-// compact LLR array, then the cover kernel (lr_cover.cu).
+// compact LLR array, then a cover kernel (lr_cover_w.cu by default, or the
+// tile cover of lr_cover.cu when the shape asks for it).
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "lr_internal.h"
@@ -9,10 +10,12 @@ namespace lr {
 
 cudaError_t configure_front();
 cudaError_t configure_cover();
+cudaError_t configure_cover_w();
 
 cudaError_t configure_kernels() {
     cudaError_t e = configure_front();
-    return e == cudaSuccess ? configure_cover() : e;
+    if (e == cudaSuccess) e = configure_cover();
+    return e == cudaSuccess ? configure_cover_w() : e;
 }
 
 cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
@@ -35,7 +38,10 @@ cudaError_t launch_query(const int32_t* sa, const int32_t* rank, const int32_t* 
         launch_gather_front(rank, lcp, n, s, segs, stream); // k_gather_llr
     }
     mark();
-    launch_cover(n, s, lr_len, lr_start, offsets, starts, capacity, all, shape.cover_tiles_per, stream);
+    if (shape.tile_cover)
+        launch_cover(n, s, lr_len, lr_start, offsets, starts, capacity, all, shape.cover_tiles_per, stream);
+    else
+        launch_cover_w(n, s, lr_len, lr_start, offsets, starts, capacity, all, stream);
     if (timed) cudaEventRecord(events->ev[k], stream);
     if (launches) *launches = (sa ? 4 : 2) + (segs.num > 0 ? 1 : 0);
     if (events) events->count = k;

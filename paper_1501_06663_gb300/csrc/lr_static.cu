@@ -17,11 +17,14 @@ constexpr size_t align_s(size_t v) { return (v + kAlignS - 1) / kAlignS * kAlign
 
 // Scratch layout for n <= kStaticMaxN (rank-gather front end + cover kernel).
 constexpr long long kTilesMax = (kStaticMaxN + lr::kTile - 1) / lr::kTile;
+constexpr long long kSegsMax = (kStaticMaxN + lr::kSeg - 1) / lr::kSeg;
 constexpr size_t kOffStatusG = kAlignS;                   // [0, 256): tickets, per-query and sticky error bits
 constexpr size_t kOffStatusO = align_s(kOffStatusG + (size_t)kTilesMax * 8);
-constexpr size_t kZeroEnd = kOffStatusO + (size_t)kTilesMax * 8;
+constexpr size_t kOffStatusW = align_s(kOffStatusO + (size_t)kTilesMax * 8);
+constexpr size_t kZeroEnd = kOffStatusW + (size_t)kSegsMax * 8;
 constexpr size_t kOffCbase = align_s(kZeroEnd);
-constexpr size_t kOffCstart = align_s(kOffCbase + (size_t)(kTilesMax + 1) * 4);
+constexpr size_t kOffSegCbase = align_s(kOffCbase + (size_t)(kTilesMax + 1) * 4);
+constexpr size_t kOffCstart = align_s(kOffSegCbase + (size_t)(kSegsMax + 1) * 4);
 constexpr size_t kOffCend = align_s(kOffCstart + (size_t)kStaticMaxN * 4);
 constexpr size_t kStaticBytes = align_s(kOffCend + (size_t)kStaticMaxN * 4);   // about 8.1 MB
 
@@ -68,10 +71,13 @@ extern "C" lr_status lr_query_all_static(lr_stream_t stream, const int32_t* d_ra
     s.err = reinterpret_cast<unsigned*>(b + 32);
     s.status_g = reinterpret_cast<unsigned long long*>(b + kOffStatusG);
     s.status_o = reinterpret_cast<unsigned long long*>(b + kOffStatusO);
+    s.status_w = reinterpret_cast<unsigned long long*>(b + kOffStatusW);
     s.tile_cbase = reinterpret_cast<int32_t*>(b + kOffCbase);
+    s.seg_cbase = reinterpret_cast<int32_t*>(b + kOffSegCbase);
     s.cstart = reinterpret_cast<int32_t*>(b + kOffCstart);
     s.cend = reinterpret_cast<int32_t*>(b + kOffCend);
     s.ntiles = lr::num_tiles(n);
+    s.nsegs = lr::num_segs(n);
     // what every query must find at zero: tickets, both error words, the
     // look-back words of both kernels (one memset, no allocation)
     s.zero_base = b;

@@ -178,7 +178,7 @@ def test_autotune_choice_keeps_results_and_round_trips(ctx, tmp_path):
     desc = P.batch_desc(d_off, d_lcp, sa=d_sa, rank=d_rank)
     outs = _outs(n, 4 * n)
     code = P.lr_autotune(ctx.handle, desc, *outs)
-    assert code in (0, 1, 2, 3, 4, 6)
+    assert code in SHAPE_CODES
     # every shape gives the same answer: run the tuned one through the normal entry point
     got = ctx.query_batch(d_off, d_lcp, sa=d_sa, rank=d_rank)
     _assert_equal(tuple(t.cpu().numpy() for t in got), want, "tuned code %d" % code)
@@ -246,10 +246,14 @@ def test_plan_reports_capacity(ctx):
         P.lr_plan_destroy(plan)
 
 
-@pytest.mark.parametrize("code", [0, 1, 4, 2, 3, 6])
+SHAPE_CODES = [0, 2, 8, 9, 12, 10, 11, 14]
+
+
+@pytest.mark.parametrize("code", SHAPE_CODES)
 def test_every_shape_code_matches_the_oracle(ctx, code, tmp_path):
-    """Each shape the autotuner can pick (cover tile 2048 / 4096 / 8192,
-    either front end) gives the oracle's answer, single string and batch."""
+    """Each shape the autotuner can pick (warp-segment cover, or tile cover
+    with tiles of 2048 / 4096 / 8192, either front end) gives the oracle's
+    answer, single string and batch."""
     w = W.single("dna_64m", n=700_000)
     text, off, _ = W.batched_mix(count=24, lo=1024, hi=64 * 1024, seed=13)
     sa_b, rank_b, lcp_b = _batch(text, off)
@@ -283,7 +287,7 @@ def _dense_compact_text(seed, front, w=40):
     return np.concatenate([head, R, tail])
 
 
-@pytest.mark.parametrize("code", [0, 1, 4, 2, 3, 6])
+@pytest.mark.parametrize("code", SHAPE_CODES)
 def test_every_shape_code_on_tiles_of_compact_llrs(ctx, code, tmp_path):
     """Each shape code on an input whose cover tiles consist entirely of
     compact LLR's (the packed holder index of a staged 8192-position tile
