@@ -179,21 +179,30 @@ def whole_job_rate(ws: int, n: int, ms: float) -> float:
     return ws * n / (ms * 1e-3) / 1e9
 
 
-def cpu_oracle_rate(w, target_s: float, seed: int = 0):
-    """Algorithm 3 (the oracle as it stands) over a contiguous block of positions."""
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(w, target_s: float, seed: int = 0, threads: int = 1):
+    """Algorithm 3 (the oracle as it stands) over a contiguous block of
+    positions, split into `threads` disjoint sub-blocks run at the same time
+    (one host core each)."""
     import oracle
     n = w.n
     rng = np.random.default_rng(seed)
-    probe = 20000
+    probe = 20000 * threads
     a = int(rng.integers(0, max(1, n - probe)))
     t0 = time.perf_counter()
-    oracle.lr_at(w.rank, w.lcp, np.arange(a, min(n, a + probe)))
+    oracle.lr_at_range(w.rank, w.lcp, a, min(n, a + probe), threads=threads)
     dt = max(time.perf_counter() - t0, 1e-4)
     block = int(min(n, max(probe, probe * target_s / dt)))
     a = int(rng.integers(0, max(1, n - block)))
-    ks = np.arange(a, a + block, dtype=np.int64)
     t0 = time.perf_counter()
-    oracle.lr_at(w.rank, w.lcp, ks)
+    oracle.lr_at_range(w.rank, w.lcp, a, a + block, threads=threads)
     dt = time.perf_counter() - t0
     return block / dt / 1e9, block, a, dt
 
@@ -260,11 +269,32 @@ def batched_leg(lr, dev, stream, count: int, reps: int):
 
     import workloads as W
     text, off, _ = W.batched_mix(count=count, lo=1024, hi=4 * W.MI, seed=4)
-    sa, rank, lcp = W.prep_many(text, off)
-    del text
     total = int(off[-1])
-    d_off, d_sa, d_rank, d_lcp = (torch.from_numpy(a).to(dev) for a in (off, sa, rank, lcp))
-    del sa, rank, lcp
+    # sa / rank / lcp of every string built on the GPU (the host prep of
+    # about 2 G symbols would take minutes), checked against the host prep
+    # on a sample of strings
+    d_off = torch.from_numpy(off).to(dev)
+    d_text = torch.from_numpy(text).to(dev)
+    builder = lr.Context(dev.index)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    d_sa, d_rank, d_lcp = builder.build_arrays_batch(d_off, d_text, stream=stream)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    builder.close()
+    del d_text
+    torch.cuda.empty_cache()
+    sample = np.random.default_rng(44).choice(count, min(16, count), replace=False)
+    build_ok = True
+    for j in sample:
+        a, b = int(off[j]), int(off[j + 1])
+        if b > a:
+            h_sa, h_rank, h_lcp = W.prep(text[a:b])
+            build_ok &= bool(np.array_equal(d_sa[a:b].cpu().numpy(), h_sa)
+                             and np.array_equal(d_rank[a:b].cpu().numpy(), h_rank)
+                             and np.array_equal(d_lcp[a + j:b + j + 1].cpu().numpy(), h_lcp))
+    del text
+    if not build_ok:
+        raise RuntimeError("batched leg: GPU-built arrays differ from the host prep")
     ln = torch.empty(total, dtype=torch.int32, device=dev)
     st = torch.empty(total, dtype=torch.int32, device=dev)
     offs = torch.empty(total + 1, dtype=torch.int64, device=dev)
@@ -312,8 +342,14 @@ def batched_leg(lr, dev, stream, count: int, reps: int):
         raise RuntimeError("batched leg: device error in the per-string loop")
     lr.lr_destroy(ctx)
     g = lambda ms: round(total / (ms * 1e-3) / 1e9, 3)
+    peak, peak_kind = measured_peaks()
+    path_bytes = 4.0 * total + 4.0 * (total + count) + 16.0 * total + 8.0 * (total + 1) + 4.0 * tot
+    frac = lambda ms: round(path_bytes / (ms * 1e-3) / 1e9 / peak, 4)
     return {"workload": "batched mix: %d strings, log-uniform lengths 1Ki-4Mi (seed 4)" % count,
             "positions": total, "lr_starts": tot, "reps": reps,
+            "arrays": {"built_on": "GPU (lr_batch_build_arrays)", "ms": round(build_ms, 1),
+                       "equal_to_host_prep": "checked on %d strings" % len(sample)},
+            "path_roofline_frac": {"batched": frac(batched_ms), "autotuned": frac(tuned_ms), "peak_kind": peak_kind},
             "batched": {"ms": round(batched_ms, 3), "value": g(batched_ms)},
             "autotuned": {"ms": round(tuned_ms, 3), "value": g(tuned_ms), "shape_code": code},
             "captured_plan": {"ms": round(plan_ms, 3), "value": g(plan_ms)},
@@ -452,6 +488,51 @@ def serving_leg(lr, dev, count: int, loads, seed: int = 5):
             "saturation": sat["value"], "one_job_per_call_saturation": plain_sat["value"],
             "p50_ms": mid["ours"]["p50_ms"], "p99_ms": mid["ours"]["p99_ms"], "at_offered_load": mid["offered_load"],
             "sweep": sweep, "text_jobs": text_jobs}
+
+
+def single_leg(lr, dev, stream, name: str, steps: int, warmup: int):
+    """One lr_query_all per step on another single-string workload (sa + lcp
+    resident), with its whole-path roofline."""
+    import torch
+
+    import workloads as W
+    w = W.single(name)
+    n = w.n
+    d_sa = torch.from_numpy(w.sa).to(dev)
+    d_lcp = torch.from_numpy(w.lcp).to(dev)
+    ln = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ctx = lr.lr_create(dev.index)
+    s0, total = lr.lr_query_all(ctx, d_sa, None, d_lcp, ln, st, off, torch.empty(1, dtype=torch.int32, device=dev),
+                                stream)
+    if s0 not in (lr.LR_OK, lr.LR_ERR_CAPACITY):
+        raise lr.LRError(s0, "lr_query_all (%s)" % name)
+    starts = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+
+    def step():
+        r, _ = lr.lr_query_all(ctx, d_sa, None, d_lcp, ln, st, off, starts, stream, sync=False)
+        if r != lr.LR_OK:
+            raise lr.LRError(r, "lr_query_all (%s)" % name)
+
+    ms = _event_ms(stream, step, steps, warm=warmup)
+    lr.lr_set_phase_timing(ctx, True)
+    step()
+    phases = lr.lr_phase_times(ctx)
+    lr.lr_set_phase_timing(ctx, False)
+    if lr.lr_device_status(ctx, stream) != lr.LR_OK:
+        raise RuntimeError("%s: device error" % name)
+    lr.lr_destroy(ctx)
+    peak, peak_kind = measured_peaks()
+    path_bytes = 4.0 * n + 4.0 * (n + 1) + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
+    inputs_mb = (8 * n + 4) / 1e6
+    return {"workload": name, "n": n, "ms_per_step": round(ms, 4), "value": round(n / (ms * 1e-3) / 1e9, 3),
+            "unit": UNIT, "steps": steps, "total_lr_starts": total,
+            "kernel_ms": {nm: round(p, 4) for nm, p in zip(["partition", "bucket_llr", "cover"], phases or [])},
+            "path_roofline": {"achieved": round(path_bytes / (ms * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(path_bytes / (ms * 1e-3) / 1e9 / peak, 4), "peak_kind": peak_kind},
+            "l2": "inputs %.0f MB: %s" % (inputs_mb, "larger than the 129 MB L2" if inputs_mb > 129 else
+                                          "fit in the 129 MB L2 (warm between steps)")}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -663,6 +744,11 @@ def run_ours(args):
     del d_sa, d_rank, d_lcp, ln, st, off, starts
     torch.cuda.empty_cache()
     batched = serving = None
+    others = []
+    if rank == 0:
+        for name in [x for x in args.extra_workloads.split(",") if x]:
+            others.append(single_leg(lr, dev, stream, name, max(3, min(args.steps, 20)), 3))
+            torch.cuda.empty_cache()
     if rank == 0 and args.batched_count > 0:
         batched = batched_leg(lr, dev, stream, args.batched_count, max(3, min(args.steps, 10)))
         torch.cuda.empty_cache()
@@ -688,7 +774,9 @@ def run_ours(args):
         path_bytes = 4.0 * n + 4.0 * (n + 1) + 4.0 * n + 4.0 * n + 8.0 * (n + 1) + 4.0 * total
         path_achieved = path_bytes / (ms * 1e-3) / 1e9
         value = whole_job_rate(ws, n, ms)
-        rate, block, a0, dt = cpu_oracle_rate(w, args.cpu_seconds)
+        cores = host_cores()
+        rate, block, a0, dt = cpu_oracle_rate(w, args.cpu_seconds, threads=cores)
+        rate1, block1, a1, dt1 = cpu_oracle_rate(w, args.cpu_seconds / 4, seed=1, threads=1)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -717,9 +805,14 @@ def run_ours(args):
                                   "value": round(whole_job_rate(ws, n, gather_ms), 3),
                                   "kernel_ms": {nm: round(p, 4) for nm, p in
                                                 zip(["gather_llr", "cover"], per_gather)}},
-            "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
-                                       "[%d, %d) of the same workload, %.1f s single-threaded" % (a0, a0 + block, dt)},
+                                       "[%d, %d) of the same workload, split into %d blocks run at once on the "
+                                       "host cores, %.1f s" % (a0, a0 + block, cores, dt)},
+            "cpu_baseline_single_core": {"value": round(rate1, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                         "sample": "Algorithm 3 on positions [%d, %d), one thread, %.1f s"
+                                                   % (a1, a1 + block1, dt1)},
+            "other_workloads": others,
             "e2e": {"value": round(whole_job_rate(ws, n, e2e_ms), 3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d_step,
                     "d2h_bytes_per_step": d2h_step,
@@ -746,11 +839,12 @@ def run_reference(args):
         return
     import workloads as W
     w = W.single(args.workload, args.n)
+    cores = host_cores()
     for _ in range(args.warmup):
-        cpu_oracle_rate(w, 0.5, seed=1)
+        cpu_oracle_rate(w, 0.5, seed=1, threads=cores)
     rates, blocks, secs = [], 0, 0.0
     for k in range(args.steps):
-        rate, block, a0, dt = cpu_oracle_rate(w, args.ref_step_seconds, seed=100 + k)
+        rate, block, a0, dt = cpu_oracle_rate(w, args.ref_step_seconds, seed=100 + k, threads=cores)
         blocks += block
         secs += dt
     value = blocks / secs / 1e9
@@ -759,8 +853,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "n": w.n, "parallelism": "single"},
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "Algorithm 3 on %d random contiguous blocks, %d positions in total" % (args.steps, blocks)},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "Algorithm 3 on %d random contiguous blocks, %d positions in total, each block "
+                                   "split into %d sub-blocks run at once on the host cores" % (args.steps, blocks, cores)},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -779,8 +874,10 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=2.0)
     ap.add_argument("--e2e-inflight", type=int, default=3,
                     help="host-buffer queries in flight at once in the e2e measurement")
-    ap.add_argument("--batched-count", type=int, default=512,
+    ap.add_argument("--batched-count", type=int, default=4096,
                     help="strings of the batched leg (4096 = the full batched mix; 0 = skip)")
+    ap.add_argument("--extra-workloads", default="dna_iid_1m,dna_64m",
+                    help="other single-string workloads timed after the main one (comma-separated; empty = none)")
     ap.add_argument("--serving-jobs", type=int, default=2000, help="jobs in the serving pool (0 = skip)")
     ap.add_argument("--serving-loads", default="0.2,0.4,0.6,0.8,1.0,1.2",
                     help="offered loads, as fractions of the serving loop's saturation throughput")

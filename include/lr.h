@@ -155,8 +155,12 @@ lr_status lr_query_all_host(lr_ctx* ctx, lr_stream_t stream,
  * Work memory, about (37 + 4 R) bytes per position for R doubling rounds
  * (R is about log2 of the longest repeat / c, plus 2, c = 7 .. 63 symbols
  * per round-0 key by the alphabet size), is kept in the
- * context and grown on demand (LR_ERR_NOMEM when it does not fit).  Both
- * calls wait for `stream` (once per round); *rounds (may be NULL) receives R.
+ * context and grown on demand (LR_ERR_NOMEM when it does not fit).  A batch
+ * of more than 2^29 positions is built in chunks of whole strings of at
+ * most 2^29 positions (one string longer than that is a chunk of its own),
+ * so its work memory follows the chunk; its offset table is then also
+ * checked on the host.  Both calls wait for `stream` (once per round);
+ * *rounds (may be NULL) receives R (the largest over the chunks).
  * An offset table that does not start at 0, end at total or never
  * decrease is reported as LR_ERR_SENTINEL before any symbol is read.
  */

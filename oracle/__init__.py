@@ -20,6 +20,8 @@ lr_leftmost_compact    Algorithm 2
 lr_all_raw             Algorithm 3 (appendix)
 lr_all_compact         Algorithm 4 (appendix)
 lr_at                  Algorithm 3 for sampled positions only
+lr_at_range            Algorithm 3 for a range of positions (lr_at on disjoint
+                       blocks at once, one thread each)
 brute                  Definition 1 / the problem statement of Sec. 2, from the
                        string alone (O(n^2) suffix-pair comparison)
 definition.lr_all      Definition 1 by enumerating every substring (tiny n)
@@ -193,6 +195,34 @@ def lr_at(rank, lcp, ks):
         raise ValueError("sample position out of range")
     nk = int(ks.size)
     return _csr_call(_L().oracle_lr_at, nk, (_p(rank), _p(lcp), n, _p(ks), nk), 4 * nk)
+
+
+def lr_at_range(rank, lcp, a: int, b: int, threads: int = 1):
+    """Algorithm 3 for every position of [a, b), as CSR over those positions.
+
+    Each position's two walks are independent of every other position's
+    (Sec. 3), so the range is split into `threads` contiguous blocks that
+    run ``lr_at`` at the same time in threads (the C call releases the
+    interpreter lock); the blocks' results are concatenated in order.  The
+    arithmetic is ``lr_at``'s, unchanged.
+    """
+    import concurrent.futures as cf
+    rank, lcp, n = _check_inputs(rank, lcp)
+    a, b = max(0, int(a)), min(n, int(b))
+    if b <= a:
+        return (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(1, np.int64), np.zeros(0, np.int32))
+    threads = max(1, min(int(threads), b - a))
+    cuts = np.linspace(a, b, threads + 1).astype(np.int64)
+    blocks = [(int(cuts[i]), int(cuts[i + 1])) for i in range(threads) if cuts[i + 1] > cuts[i]]
+    with cf.ThreadPoolExecutor(len(blocks)) as ex:
+        parts = list(ex.map(lambda ab: lr_at(rank, lcp, np.arange(ab[0], ab[1], dtype=np.int64)), blocks))
+    ln = np.concatenate([q[0] for q in parts])
+    st = np.concatenate([q[1] for q in parts])
+    sizes = [q[3].size for q in parts]
+    base = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    off = np.concatenate([[0]] + [q[2][1:] + base[i] for i, q in enumerate(parts)]).astype(np.int64)
+    starts = np.concatenate([q[3] for q in parts]).astype(np.int32)
+    return ln, st, off, starts
 
 
 def walk_counts(rank, lcp):

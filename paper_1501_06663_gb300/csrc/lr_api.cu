@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <map>
 #include <new>
+#include <vector>
 #include "lr.h"
 #include "lr_internal.h"
 #include "lr_device.cuh"
@@ -29,6 +30,8 @@ struct lr_ctx {
     std::map<int, int> tuned;             // shape class -> shape code (lr_autotune)
     lr::IndexWork index_work;             // work memory of lr_build_arrays / lr_batch_build_arrays
     int64_t* d_off2 = nullptr;            // {0, n} for single-string builds
+    int64_t* d_chunk_off = nullptr;       // rebased offsets of one chunk of a large batched build
+    long long chunk_off_cap = 0;          // entries d_chunk_off holds
     int spin_limit = lr::kSpinLimit;      // look-back poll limit of this context's queries
     long long hold_tile = -1;             // test hook (lr_test_hold_lookback): cover tile kept unpublished
 };
@@ -49,6 +52,7 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr long long kMaxN = 2147483646LL;  // lcp needs n+1 int32 entries
+constexpr long long kBuildChunk = 1LL << 29; // positions per chunk of a large batched array build
 
 // Makes ctx->device current for the scope and restores the caller's device.
 struct DeviceGuard {
@@ -285,6 +289,7 @@ lr_status lr_destroy(lr_ctx* ctx) {
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     ctx->index_work.release();
     if (ctx->d_off2) cudaFree(ctx->d_off2);
+    if (ctx->d_chunk_off) cudaFree(ctx->d_chunk_off);
     if (ctx->events_created)
         for (int i = 0; i <= lr::kMaxPhases; ++i) cudaEventDestroy(ctx->events.ev[i]);
     delete ctx;
@@ -511,16 +516,57 @@ lr_status lr_batch_build_arrays(lr_ctx* ctx, lr_stream_t stream, const lr_text_b
         return LR_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return cuda_fail(ctx, cudaErrorInvalidDevice);
-    lr_status st = index_work_for(ctx, batch->total);
-    if (st != LR_OK) return st;
     cudaStream_t strm = (cudaStream_t)stream;
     int r = 0;
-    cudaError_t e = lr::build_arrays_batch(batch->d_text, batch->total, batch->d_off, batch->num, d_sa, d_rank,
-                                           d_lcp, ctx->index_work, true, strm, &r);
+    if (batch->total <= kBuildChunk) {
+        lr_status st = index_work_for(ctx, batch->total);
+        if (st != LR_OK) return st;
+        cudaError_t e = lr::build_arrays_batch(batch->d_text, batch->total, batch->d_off, batch->num, d_sa, d_rank,
+                                               d_lcp, ctx->index_work, true, strm, &r);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
+        st = index_status(ctx, e);
+        if (st == LR_OK && rounds) *rounds = r;
+        return st;
+    }
+    // A large batch is built in chunks of whole strings of at most
+    // kBuildChunk positions (strings are independent), so that the work
+    // memory follows the chunk, not the batch.  The offset table is read
+    // back and checked on the host first.
+    const long long num = batch->num;
+    std::vector<int64_t> h(num + 1);
+    cudaError_t e = cudaMemcpyAsync(h.data(), batch->d_off, (size_t)(num + 1) * 8, cudaMemcpyDeviceToHost, strm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(strm);
-    st = index_status(ctx, e);
-    if (st == LR_OK && rounds) *rounds = r;
-    return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    if (h[0] != 0 || h[num] != batch->total) return LR_ERR_SENTINEL;
+    for (long long j = 0; j < num; ++j)
+        if (h[j + 1] < h[j]) return LR_ERR_SENTINEL;
+    if (ctx->chunk_off_cap < num + 1) {
+        if (ctx->d_chunk_off) { cudaFree(ctx->d_chunk_off); ctx->d_chunk_off = nullptr; ctx->chunk_off_cap = 0; }
+        e = cudaMalloc((void**)&ctx->d_chunk_off, (size_t)(num + 1) * 8);
+        if (e != cudaSuccess) { cudaGetLastError(); return LR_ERR_NOMEM; }
+        ctx->chunk_off_cap = num + 1;
+    }
+    std::vector<int64_t> rebased(num + 1);
+    int max_r = 0;
+    for (long long j0 = 0; j0 < num;) {
+        long long j1 = j0 + 1;
+        while (j1 < num && h[j1 + 1] - h[j0] <= kBuildChunk) ++j1;
+        const long long ct = h[j1] - h[j0];
+        for (long long j = j0; j <= j1; ++j) rebased[j - j0] = h[j] - h[j0];
+        lr_status st = index_work_for(ctx, ct > 0 ? ct : 1);
+        if (st != LR_OK) return st;
+        e = cudaMemcpyAsync(ctx->d_chunk_off, rebased.data(), (size_t)(j1 - j0 + 1) * 8, cudaMemcpyHostToDevice, strm);
+        if (e == cudaSuccess)
+            e = lr::build_arrays_batch(batch->d_text + h[j0], ct, ctx->d_chunk_off, j1 - j0, d_sa + h[j0],
+                                       d_rank + h[j0], d_lcp + h[j0] + j0, ctx->index_work, true, strm, &r);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(strm);   // the host offsets are reused next chunk
+        st = index_status(ctx, e);
+        if (st != LR_OK) return st;
+        max_r = r > max_r ? r : max_r;
+        j0 = j1;
+    }
+    if (rounds) *rounds = max_r;
+    return LR_OK;
 }
 
 lr_status lr_query_all_raw(lr_ctx* ctx, lr_stream_t stream, const int32_t* d_rank, const int32_t* d_lcp, int32_t n,

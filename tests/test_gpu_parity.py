@@ -1,9 +1,11 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
 
-Integer and index work: every comparison is bit-exact.  Small inputs are
-compared in full; the full-size workloads are compared on sampled positions
-(Algorithm 3 per position) plus properties that hold at any size.
+Integer and index work: every comparison is bit-exact.  Every input,
+the full-size workloads included, is compared in full (Algorithm 3 per
+position at the largest sizes), plus properties that hold at any size.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -196,10 +198,17 @@ def test_long_lengths_escape_16_bits(ctx):
 
 
 @pytest.mark.parametrize("name", ["dna_64m", "english_256m"])
-def test_full_size_sampled(ctx, name):
+def test_full_size_exact(ctx, name):
+    """Every position of the full-size workloads (64 Mi planted-repeat DNA,
+    256 Mi english) against Algorithm 3, run on all host cores over disjoint
+    blocks of positions; both front ends; plus the size-independent
+    properties."""
     w = W.single(name)
     got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa")
-    _sampled_check(ctx, w, got, 4000, 17)
+    want = oracle.lr_at_range(w.rank, w.lcp, 0, w.n, threads=os.cpu_count() or 1)
+    _assert_csr_equal(got, want, name)
+    del want
+    _sampled_check(ctx, w, got, 200, 17)
     got2 = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
     for a, b in zip(got, got2):
         assert np.array_equal(a, b)

@@ -351,3 +351,20 @@ def test_prep_many_matches_per_string_prep():
         s1, r1, l1 = W.prep(text[a:a + m])
         assert np.array_equal(sa[a:a + m], s1) and np.array_equal(rank[a:a + m], r1)
         assert np.array_equal(lcp[a + j:a + j + m + 1], l1)
+
+
+def test_lr_at_range_equals_the_full_run():
+    """The block-parallel driver of Algorithm 3 (lr_at on disjoint blocks at
+    once) gives the full run's CSR, for any split, and a sub-range's CSR."""
+    w = W.single("english_256m", n=200_000)
+    full = oracle.lr_all_raw(w.rank, w.lcp)
+    for threads in (1, 3, 8):
+        got = oracle.lr_at_range(w.rank, w.lcp, 0, w.n, threads=threads)
+        for a, b in zip(got, full):
+            assert np.array_equal(a, b)
+    got = oracle.lr_at_range(w.rank, w.lcp, 1234, 5678, threads=4)
+    ks = np.arange(1234, 5678)
+    for a, b in zip(got, oracle.lr_at(w.rank, w.lcp, ks)):
+        assert np.array_equal(a, b)
+    empty = oracle.lr_at_range(w.rank, w.lcp, 10, 10, threads=4)
+    assert empty[0].size == 0 and empty[2].tolist() == [0]
