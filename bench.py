@@ -705,6 +705,7 @@ def run_ours(args):
     # copies and kernels: whole-job throughput of back-to-back queries
     inflight = max(1, args.e2e_inflight)
     e2e_ms = e2e_single_ms
+    e2e_multi_ms = None
     if inflight > 1:
         ctxs = [ctx] + [lr.lr_create(local) for _ in range(inflight - 1)]
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(inflight - 1)]
@@ -733,10 +734,11 @@ def run_ours(args):
             th.start()
         for th in threads:
             th.join()
-        e2e_ms = (time.perf_counter() - t0) * 1e3 / (e2e_steps * inflight)
+        e2e_multi_ms = (time.perf_counter() - t0) * 1e3 / (e2e_steps * inflight)
         if errors:
             raise lr.LRError(errors[0], "lr_query_all_host (concurrent)")
-        e2e_ms = max_over_ranks(e2e_ms, dev)
+        e2e_multi_ms = max_over_ranks(e2e_multi_ms, dev)
+        e2e_ms = min(e2e_ms, e2e_multi_ms)           # the faster way to drive the same call
         for c in ctxs[1:]:
             lr.lr_destroy(c)
     lr.lr_destroy(ctx)
@@ -816,8 +818,10 @@ def run_ours(args):
             "e2e": {"value": round(whole_job_rate(ws, n, e2e_ms), 3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d_step,
                     "d2h_bytes_per_step": d2h_step,
-                    "steps_in_flight": inflight,
+                    "steps_in_flight": inflight if e2e_multi_ms is not None and e2e_ms == e2e_multi_ms else 1,
                     "one_in_flight": round(whole_job_rate(ws, n, e2e_single_ms), 3),
+                    "%d_in_flight" % inflight: (round(whole_job_rate(ws, n, e2e_multi_ms), 3)
+                                               if e2e_multi_ms is not None else None),
                     "host_link": link,
                     "api": "lr_query_all_host (pinned host buffers; copies and kernels inside the call)"},
             "gpu_launches": launches,

@@ -289,11 +289,13 @@ __device__ __forceinline__ PartSmem part_smem(unsigned char* raw, int nb) {
     return p;
 }
 
-// Bulk-copy staging of a level-1 round: sa[r0, r0 + kPartRound) and
-// lcp[r0, r0 + kPartRound + 4) (16-byte multiples), at a 16-byte-aligned
-// offset after the counters; it overlaps the stage area, which is written
-// only after every thread has read its entries.
-constexpr int kPartLoadBytes = kPartRound * 4 + (kPartRound + 4) * 4;
+// Bulk-copy staging of a level-1 round: sa[r0, r0 + kPartRound) and the
+// round's lcp slice (kPartRound + 1 entries from a 16-byte-aligned start,
+// rounded out to 16-byte multiples: at most kPartRound + 8 entries), at a
+// 16-byte-aligned offset after the counters; it overlaps the stage area,
+// which is written only after every thread has read its entries.
+constexpr int kPartLcpCap = kPartRound + 8;
+constexpr int kPartLoadBytes = kPartRound * 4 + kPartLcpCap * 4;
 __host__ __device__ inline size_t part_load_offset(int nb) { return ((size_t)(3 * nb + 1) * 4 + 15) & ~(size_t)15; }
 
 size_t part_smem_bytes(int nb) {
@@ -365,24 +367,52 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
     const int nb = (int)s.nsupers;                    // <= 2048
     const PartSmem P = part_smem(smem_raw, nb);
     const long long r0 = (long long)blockIdx.x * kPartRound;
-    // Full rounds of a single string (16-byte-aligned inputs) arrive by two
-    // bulk copies issued before anything else; the last round and batches
-    // load per thread.
-    const bool bulk = !kBatch && tma && r0 + kPartRound + 4 <= (long long)n + 1;
+    // Full rounds (16-byte-aligned inputs) arrive by two bulk copies issued
+    // before anything else: of a single string, every round but the last;
+    // of a batch, a round that lies inside one string, its lcp slice copied
+    // from the 16-byte boundary at or below its first entry (shift entries
+    // earlier).  Other rounds load per thread.
     const int32_t* Ssa = reinterpret_cast<const int32_t*>(smem_raw + part_load_offset(nb));
     const int32_t* Slcp = Ssa + kPartRound;
-    if (bulk && threadIdx.x == 0) {
-        mbar_init(&load_bar, 1);
-        mbar_fence_init();
-        mbar_arrive_tx(&load_bar, (unsigned)kPartLoadBytes);
-        bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
-        bulk_g2s(const_cast<int32_t*>(Slcp), lcp + r0, (kPartRound + 4) * 4, &load_bar);
+    __shared__ int bulk_s, shift_s;
+    __shared__ long long bbase_s, bnj_s;          // batch round: its string's offset and length
+    if (threadIdx.x == 0) {
+        int bk = 0, shift = 0;
+        long long lsrc = r0, cnt = kPartRound + 4;    // lcp entries copied
+        if constexpr (!kBatch) {
+            bk = tma && r0 + kPartRound + 4 <= (long long)n + 1;
+        } else if (tma && r0 + kPartRound <= (long long)n) {
+            const long long j = s.tile_seg[r0 / kTile];
+            if (j >= 0 && j < segs.num) {
+                const long long b0 = __ldg(segs.off + j), b1 = __ldg(segs.off + j + 1);
+                const long long l0 = r0 + j;          // the round's first lcp entry
+                lsrc = l0 & ~3LL;
+                cnt = (l0 + kPartRound + 1 - lsrc + 3) & ~3LL;
+                if (b0 <= r0 && r0 + kPartRound <= b1 && lsrc + cnt <= (long long)n + segs.num) {
+                    bk = 1;
+                    shift = (int)(l0 - lsrc);
+                    bbase_s = b0;
+                    bnj_s = b1 - b0;
+                }
+            }
+        }
+        bulk_s = bk;
+        shift_s = shift;
+        if (bk) {
+            mbar_init(&load_bar, 1);
+            mbar_fence_init();
+            mbar_arrive_tx(&load_bar, (unsigned)(kPartRound * 4 + cnt * 4));
+            bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
+            bulk_g2s(const_cast<int32_t*>(Slcp), lcp + lsrc, (unsigned)(cnt * 4), &load_bar);
+        }
     }
     for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
     __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
     SegView sv{};
     if constexpr (kBatch) sv.stage(segs, s, r0, (r0 + kPartRound < n) ? r0 + kPartRound : n, seg_sh);
     __syncthreads();
+    const bool bulk = bulk_s != 0;
+    const int shift = shift_s;
     unsigned bad = 0;
     if (!kBatch && blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
     // In a batch, flattened rank index r of string j is local rank
@@ -403,11 +433,19 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             const int x = j * kPartThreads + (int)threadIdx.x;
             if (!landed) { p[j] = 0xffffffffu; L[j] = 0; continue; }
             uint32_t pl = (uint32_t)Ssa[x];
-            const int32_t a = Slcp[x], c = Slcp[x + 1];
+            const int32_t a = Slcp[shift + x], c = Slcp[shift + x + 1];
             int32_t Lj = a > c ? a : c;
-            if (pl >= (uint32_t)n) { bad = 1; pl = 0xffffffffu; }
-            else if (Lj < 0 || (long long)Lj > (long long)n - pl) { bad = 1; Lj = 0; }
-            p[j] = pl;
+            if constexpr (kBatch) {
+                const long long base = bbase_s, nj = bnj_s;
+                if ((r == base && a != 0) || (r == base + nj - 1 && c != 0)) bad = 1;   // lcp sentinels
+                if (pl >= (uint32_t)nj) { bad = 1; pl = 0xffffffffu; }
+                else if (Lj < 0 || (long long)Lj > nj - pl) { bad = 1; Lj = 0; }
+                p[j] = (pl == 0xffffffffu) ? pl : (uint32_t)(base + pl);
+            } else {
+                if (pl >= (uint32_t)n) { bad = 1; pl = 0xffffffffu; }
+                else if (Lj < 0 || (long long)Lj > (long long)n - pl) { bad = 1; Lj = 0; }
+                p[j] = pl;
+            }
             L[j] = Lj;
         } else if (r < n) {
             uint32_t pl = (uint32_t)__ldcs(sa + r);
@@ -667,13 +705,12 @@ size_t bucket_smem_bytes() { return (size_t)kBucket * 2 + (size_t)(kBucket / kWa
 void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
                       cudaStream_t stream) {
     const unsigned g1 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
-    if (segs.num > 0) {
-        k_part1<true><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, 0);
-    } else {
-        // bulk copies need 16-byte-aligned sources
-        const int tma = (((uintptr_t)sa | (uintptr_t)lcp) & 15u) == 0 ? 1 : 0;
+    // bulk copies need 16-byte-aligned sources
+    const int tma = (((uintptr_t)sa | (uintptr_t)lcp) & 15u) == 0 ? 1 : 0;
+    if (segs.num > 0)
+        k_part1<true><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, tma);
+    else
         k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, tma);
-    }
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
     k_part2<<<g2, kPartThreads, part2_smem_bytes(), stream>>>(n, s);
 }
