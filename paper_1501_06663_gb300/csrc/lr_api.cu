@@ -86,7 +86,7 @@ Layout layout_for(long long n) {
     L.off_status_b = align_up(L.off_status_g + (size_t)nt * 8);
     L.off_status_o = align_up(L.off_status_b + (size_t)nb * 8);
     L.off_status_w = align_up(L.off_status_o + (size_t)nt * 8);
-    L.off_cursor1 = align_up(L.off_status_w + (size_t)ng * 8);
+    L.off_cursor1 = align_up(L.off_status_w + (size_t)lr::num_seg_tiles(n) * 8);
     L.off_cursor2 = align_up(L.off_cursor1 + (size_t)ns * 4 * lr::kCursorStride);
     L.zero_end = L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride;
     L.off_tile_cbase = align_up(L.zero_end);

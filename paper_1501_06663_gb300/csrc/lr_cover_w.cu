@@ -48,7 +48,7 @@ namespace lr {
 namespace {
 
 constexpr int kRuns = kSeg / kWarp;          // 8 runs of 32 positions per segment
-constexpr int kSegWarps = 16;                // warps (segments) per CTA
+constexpr int kSegWarps = kSegTile / kSeg;   // warps (segments) per CTA: 16
 constexpr int kSegThreads = kSegWarps * kWarp;
 constexpr int kCarry = 64;                   // carry entries a segment stages
 constexpr int kCapW = kSeg + kCarry;         // staged entries: at most one start per position + the carry

@@ -15,6 +15,7 @@ constexpr int kThreads = 256;        // threads per tile CTA
 // granularity of seg_cbase.
 constexpr int kSegLog = 8;
 constexpr int kSeg = 1 << kSegLog;   // positions per warp segment
+constexpr int kSegTile = 4096;       // positions per CTA of the warp-segment cover (its look-back unit)
 
 // Rank-order front end: a two-level radix partition of <position, L> by the
 // position, into super-buckets of 2^20 and then buckets of 2^15 positions.
@@ -55,7 +56,7 @@ struct Scratch {
     int32_t* halo;                 // nbuckets + 1: L of the position before each bucket
     int32_t* tile_seg;             // ntiles: first string overlapping each tile (batched queries)
     int32_t* seg_cbase;            // nsegs + 1: compact LLR's starting before segment j (kSeg positions)
-    unsigned long long* status_w;  // look-back words of the warp-segment cover kernel (per segment)
+    unsigned long long* status_w;  // look-back words of the warp-segment cover kernel (per kSegTile tile)
     long long ntiles;
     long long nsegs;
     long long nbuckets;
@@ -71,6 +72,7 @@ __host__ __device__ inline long long num_cover_tiles(long long n, int tiles_per)
     return (n + (long long)kTile * tiles_per - 1) / ((long long)kTile * tiles_per);
 }
 __host__ __device__ inline long long num_segs(long long n) { return (n + kSeg - 1) / kSeg; }
+__host__ __device__ inline long long num_seg_tiles(long long n) { return (n + kSegTile - 1) / kSegTile; }
 inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
 inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
 

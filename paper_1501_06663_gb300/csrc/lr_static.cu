@@ -21,7 +21,7 @@ constexpr long long kSegsMax = (kStaticMaxN + lr::kSeg - 1) / lr::kSeg;
 constexpr size_t kOffStatusG = kAlignS;                   // [0, 256): tickets, per-query and sticky error bits
 constexpr size_t kOffStatusO = align_s(kOffStatusG + (size_t)kTilesMax * 8);
 constexpr size_t kOffStatusW = align_s(kOffStatusO + (size_t)kTilesMax * 8);
-constexpr size_t kZeroEnd = kOffStatusW + (size_t)kSegsMax * 8;
+constexpr size_t kZeroEnd = kOffStatusW + (size_t)((kStaticMaxN + lr::kSegTile - 1) / lr::kSegTile) * 8;
 constexpr size_t kOffCbase = align_s(kZeroEnd);
 constexpr size_t kOffSegCbase = align_s(kOffCbase + (size_t)(kTilesMax + 1) * 4);
 constexpr size_t kOffCstart = align_s(kOffSegCbase + (size_t)(kSegsMax + 1) * 4);

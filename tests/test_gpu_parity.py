@@ -201,13 +201,21 @@ def test_long_lengths_escape_16_bits(ctx):
 def test_full_size_exact(ctx, name):
     """Every position of the full-size workloads (64 Mi planted-repeat DNA,
     256 Mi english) against Algorithm 3, run on all host cores over disjoint
-    blocks of positions; both front ends; plus the size-independent
+    blocks of positions: the all-LR query with both front ends, the
+    leftmost-only query and the raw-LLR variant; plus the size-independent
     properties."""
     w = W.single(name)
     got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa")
     want = oracle.lr_at_range(w.rank, w.lcp, 0, w.n, threads=os.cpu_count() or 1)
     _assert_csr_equal(got, want, name)
-    del want
+    # the leftmost-only query (Algorithm 2's output) and the raw-LLR variant
+    # (Algorithms 1 and 3, no compaction) against the same oracle run
+    st, ln = ctx.query_leftmost(_dev(w.lcp), sa=_dev(w.sa))
+    assert np.array_equal(ln.cpu().numpy(), want[0]) and np.array_equal(st.cpu().numpy(), want[1])
+    del st, ln
+    raw = tuple(t.cpu().numpy() for t in ctx.query_all_raw(_dev(w.lcp), _dev(w.rank)))
+    _assert_csr_equal(raw, want, name + " raw")
+    del want, raw
     _sampled_check(ctx, w, got, 200, 17)
     got2 = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
     for a, b in zip(got, got2):
