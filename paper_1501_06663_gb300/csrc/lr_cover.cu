@@ -4,7 +4,7 @@
 //
 // Starts and ends of LLRc strictly increase (Sec. 3.2), so the compact LLR's
 // covering a position k form a contiguous window of LLRc whose two ends only
-// move right as k grows.  Per tile of 2048 or 4096 positions (tiles in
+// move right as k grows.  Per tile of 2048, 4096 or 8192 positions (tiles in
 // order by an atomic ticket):
 //
 //  * the window range of the whole tile is LLRc[lo, cb1): the tile's own
@@ -15,8 +15,10 @@
 //  * for position k the window is [lo_k, hi_k] with hi_k = (starts <= k) - 1
 //    and lo_k = (ends < k) in carry ++ local numbering: two prefix popcounts,
 //    no binary search (the paper's per-position binary search);
-//  * one walk over the window gives the longest length, the leftmost start
-//    and the number of ties (Algorithm 2's walk, with Algorithm 4's count);
+//  * the longest length, the leftmost start and the ties of every window
+//    (Algorithm 2's walk, with Algorithm 4's count) come from a range-maximum
+//    table built per run of 32 positions over the run's entries (a walk over
+//    the window when the run spans more than 32 entries);
 //  * for the all-LR query, the tie counts are scanned (block scan plus a
 //    decoupled look-back over the tiles) into CSR offsets, and a second walk
 //    writes every start of the longest length, ascending (Algorithm 4's
