@@ -222,6 +222,23 @@ def test_full_size_exact(ctx, name):
         assert np.array_equal(a, b)
 
 
+def test_513_super_buckets(ctx):
+    """n = 2^29 + 12345 planted-repeat DNA: the first partition level spreads
+    the rank-order entries over 513 super-buckets of 2^20 positions, the last
+    of them (and its last bucket of 2^15) ragged.  Every position against
+    Algorithm 3."""
+    n = (1 << 29) + 12345
+    free, _ = torch.cuda.mem_get_info()
+    if free < n * 64:
+        pytest.skip("needs %.0f GB free" % (n * 64 / 1e9))
+    text = W.make_text("dna", n, 21)
+    sa, rank, lcp = W.prep(text)
+    del text
+    got = _gpu_all(ctx, sa, rank, lcp, "sa")
+    want = oracle.lr_at_range(rank, lcp, 0, n, threads=os.cpu_count() or 1)
+    _assert_csr_equal(got, want, "n = 2^29 + 12345")
+
+
 # ------------------------------------------------------------------ API behaviour
 
 def test_capacity_error_keeps_offsets(ctx):
