@@ -381,19 +381,18 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
         long long lsrc = r0, cnt = kPartRound + 4;    // lcp entries copied
         if constexpr (!kBatch) {
             bk = tma && r0 + kPartRound + 4 <= (long long)n + 1;
-        } else if (tma && r0 + kPartRound <= (long long)n) {
-            const long long j = s.tile_seg[r0 / kTile];
-            if (j >= 0 && j < segs.num) {
-                const long long b0 = __ldg(segs.off + j), b1 = __ldg(segs.off + j + 1);
-                const long long l0 = r0 + j;          // the round's first lcp entry
-                lsrc = l0 & ~3LL;
-                cnt = (l0 + kPartRound + 1 - lsrc + 3) & ~3LL;
-                if (b0 <= r0 && r0 + kPartRound <= b1 && lsrc + cnt <= (long long)n + segs.num) {
-                    bk = 1;
-                    shift = (int)(l0 - lsrc);
-                    bbase_s = b0;
-                    bnj_s = b1 - b0;
-                }
+        } else if (tma && r0 + kPartRound < (long long)n) {
+            // the round lies inside one string when the string holding its
+            // first position also holds the next round's first position (two
+            // independent loads; the string's offsets come from warp 1)
+            const long long t0 = r0 / kTile;
+            const long long j = s.tile_seg[t0], jn = s.tile_seg[t0 + kPartRound / kTile];
+            const long long l0 = r0 + j;              // the round's first lcp entry
+            lsrc = l0 & ~3LL;
+            cnt = (l0 + kPartRound + 1 - lsrc + 3) & ~3LL;
+            if (j >= 0 && j < segs.num && jn == j && lsrc >= 0 && lsrc + cnt <= (long long)n + segs.num) {
+                bk = 1;
+                shift = (int)(l0 - lsrc);
             }
         }
         bulk_s = bk;
@@ -406,13 +405,35 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             bulk_g2s(const_cast<int32_t*>(Slcp), lcp + lsrc, (unsigned)(cnt * 4), &load_bar);
         }
     }
+    if constexpr (kBatch) {
+        // the string of a round that may arrive by bulk copies: its offset
+        // and length, zero when the offset table contradicts the round (every
+        // entry then fails its checks below)
+        if (threadIdx.x == kWarp && tma && r0 + kPartRound < (long long)n) {
+            const long long j = s.tile_seg[r0 / kTile];
+            long long b0 = 0, b1 = 0;
+            if (j >= 0 && j < segs.num) { b0 = __ldg(segs.off + j); b1 = __ldg(segs.off + j + 1); }
+            const bool ok = b0 >= 0 && b0 <= r0 && b1 > r0 + kPartRound && b1 <= (long long)n;
+            bbase_s = ok ? b0 : 0;
+            bnj_s = ok ? b1 - b0 : 0;
+        }
+    }
     for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
     __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
     SegView sv{};
-    if constexpr (kBatch) sv.stage(segs, s, r0, (r0 + kPartRound < n) ? r0 + kPartRound : n, seg_sh);
     __syncthreads();
     const bool bulk = bulk_s != 0;
     const int shift = shift_s;
+    // a round across string boundaries looks its strings up per entry
+    if constexpr (kBatch) {
+        if (!bulk) sv.stage(segs, s, r0, (r0 + kPartRound < n) ? r0 + kPartRound : n, seg_sh);
+    }
+    // bulk round of a batch: its string's offset and length (the string
+    // goes on past the round, so only its first rank can lie in the round)
+    uint32_t bbase = 0, bnj = 0;
+    if constexpr (kBatch) {
+        if (bulk) { bbase = (uint32_t)bbase_s; bnj = (uint32_t)bnj_s; }
+    }
     unsigned bad = 0;
     if (!kBatch && blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
     // In a batch, flattened rank index r of string j is local rank
@@ -436,11 +457,10 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             const int32_t a = Slcp[shift + x], c = Slcp[shift + x + 1];
             int32_t Lj = a > c ? a : c;
             if constexpr (kBatch) {
-                const long long base = bbase_s, nj = bnj_s;
-                if ((r == base && a != 0) || (r == base + nj - 1 && c != 0)) bad = 1;   // lcp sentinels
-                if (pl >= (uint32_t)nj) { bad = 1; pl = 0xffffffffu; }
-                else if (Lj < 0 || (long long)Lj > nj - pl) { bad = 1; Lj = 0; }
-                p[j] = (pl == 0xffffffffu) ? pl : (uint32_t)(base + pl);
+                if (x == 0 && (long long)bbase == r0 && bnj != 0 && a != 0) bad = 1;   // lcp sentinel
+                if (pl >= bnj) { bad = 1; pl = 0xffffffffu; }
+                else if (Lj < 0 || (uint32_t)Lj > bnj - pl) { bad = 1; Lj = 0; }
+                p[j] = (pl == 0xffffffffu) ? pl : bbase + pl;
             } else {
                 if (pl >= (uint32_t)n) { bad = 1; pl = 0xffffffffu; }
                 else if (Lj < 0 || (long long)Lj > (long long)n - pl) { bad = 1; Lj = 0; }

@@ -152,6 +152,27 @@ def test_bad_offset_tables_are_reported(ctx):
     _check(ctx, text, off, fronts=("sa",))
 
 
+def test_broken_sentinels_in_bulk_rounds(ctx):
+    """Strings that start on a partition round (4096 ranks) and fill whole
+    rounds arrive by bulk copies; a string's first lcp entry that is not 0
+    is caught there, and its last one in the round that ends the string."""
+    rng = np.random.default_rng(31)
+    lens = [8192, 5 * 4096 + 100, 3000]
+    off = _offsets(lens)
+    text = _random_text(rng, int(off[-1]), 4)
+    sa, rank, lcp = _batch(text, off)
+    n = int(off[-1])
+    for where in (0, int(off[1]) + 1, int(off[2]) + 1):    # first of string 0, first and last of string 1
+        bad = lcp.copy()
+        bad[where] = 5
+        for front in ("sa", "rank"):
+            kw = {"sa": _dev(sa)} if front == "sa" else {"rank": _dev(rank)}
+            d = P.batch_desc(_dev(off), _dev(bad), **kw)
+            st, _ = P.lr_batch_query_all(ctx.handle, d, *_outs(n, 4 * n))
+            assert st == P.LR_ERR_SENTINEL, (where, front, P.status_str(st))
+    _check(ctx, text, off)
+
+
 def test_invalid_batch_descriptors(ctx):
     z = torch.zeros(8, dtype=torch.int32, device="cuda")
     o = torch.zeros(8, dtype=torch.int64, device="cuda")
