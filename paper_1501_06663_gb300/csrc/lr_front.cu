@@ -273,8 +273,9 @@ void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, con
 // contiguous run.
 struct PartSmem {
     uint32_t* hist;      // nb: entries of the round per bucket, then slot counters
+    uint32_t* loff;      // nb + 1: exclusive prefix of hist (staging offsets), in
+                         // place of hist (the scan reads hist before it writes)
     uint32_t* base;      // nb: the round's reserved offset in each bucket
-    uint32_t* loff;      // nb + 1: exclusive prefix of hist (staging offsets)
     uint32_t* stage;     // kPartRound entries in bucket order
     uint16_t* sbk;       // kPartRound bucket ids of stage[]
 };
@@ -282,9 +283,9 @@ struct PartSmem {
 __device__ __forceinline__ PartSmem part_smem(unsigned char* raw, int nb) {
     PartSmem p;
     p.hist = reinterpret_cast<uint32_t*>(raw);
-    p.base = p.hist + nb;
-    p.loff = p.base + nb;
-    p.stage = p.loff + nb + 1;
+    p.loff = p.hist;
+    p.base = p.loff + nb + 1;
+    p.stage = p.base + nb;
     p.sbk = reinterpret_cast<uint16_t*>(p.stage + kPartRound);
     return p;
 }
@@ -296,16 +297,16 @@ __device__ __forceinline__ PartSmem part_smem(unsigned char* raw, int nb) {
 // which is written only after every thread has read its entries.
 constexpr int kPartLcpCap = kPartRound + 8;
 constexpr int kPartLoadBytes = kPartRound * 4 + kPartLcpCap * 4;
-__host__ __device__ inline size_t part_load_offset(int nb) { return ((size_t)(3 * nb + 1) * 4 + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t part_load_offset(int nb) { return ((size_t)(2 * nb + 1) * 4 + 15) & ~(size_t)15; }
 
 size_t part_smem_bytes(int nb) {
-    const size_t a = (size_t)(3 * nb + 1) * 4 + (size_t)kPartRound * 6;
+    const size_t a = (size_t)(2 * nb + 1) * 4 + (size_t)kPartRound * 6;
     const size_t b = part_load_offset(nb) + kPartLoadBytes;
     return a > b ? a : b;
 }
 
 // level 2 loads per thread: counters and stage area only
-size_t part2_smem_bytes() { return (size_t)(3 * kSubPerSuper + 1) * 4 + (size_t)kPartRound * 6; }
+size_t part2_smem_bytes() { return (size_t)(2 * kSubPerSuper + 1) * 4 + (size_t)kPartRound * 6; }
 
 // Exclusive scan of hist[0..nb) into loff[0..nb] by the whole CTA
 // (kPartThreads threads, R consecutive buckets each, nb <= R * kPartThreads),
@@ -419,7 +420,10 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
         }
     }
     for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
-    __shared__ long long seg_sh[kBatch ? kSegCap + 1 : 1];
+    // a round across strings copies nothing in bulk: its string offsets use
+    // the bulk-copy area (read only before the stage area is written)
+    static_assert((kSegCap + 1) * 8 <= kPartLoadBytes, "string offsets must fit the bulk-copy area");
+    long long* seg_sh = reinterpret_cast<long long*>(smem_raw + part_load_offset(nb));
     SegView sv{};
     __syncthreads();
     const bool bulk = bulk_s != 0;
