@@ -364,47 +364,60 @@ template <bool kBatch>
 __global__ void __launch_bounds__(kPartThreads, kPartBlocks)
 k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs, int tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned long long load_bar;
+    __shared__ unsigned long long load_bar, load_bar2;
     const int nb = (int)s.nsupers;                    // <= 2048
     const PartSmem P = part_smem(smem_raw, nb);
     const long long r0 = (long long)blockIdx.x * kPartRound;
     // Full rounds (16-byte-aligned inputs) arrive by two bulk copies issued
-    // before anything else: of a single string, every round but the last;
-    // of a batch, a round that lies inside one string, its lcp slice copied
-    // from the 16-byte boundary at or below its first entry (shift entries
-    // earlier).  Other rounds load per thread.
+    // before anything else: of a single string, every round but the last.
+    // Of a batch, every full round's sa slice (flattened like the positions)
+    // at once, on its own barrier, and then the lcp slice of a round that
+    // lies inside one string, copied from the 16-byte boundary at or below
+    // its first entry (shift entries earlier).  Other rounds load per thread.
     const int32_t* Ssa = reinterpret_cast<const int32_t*>(smem_raw + part_load_offset(nb));
     const int32_t* Slcp = Ssa + kPartRound;
-    __shared__ int bulk_s, shift_s;
+    __shared__ int bulk_s, shift_s, sab_s;
     __shared__ long long bbase_s, bnj_s;          // batch round: its string's offset and length
     if (threadIdx.x == 0) {
-        int bk = 0, shift = 0;
+        int bk = 0, shift = 0, sab = 0;
         long long lsrc = r0, cnt = kPartRound + 4;    // lcp entries copied
         if constexpr (!kBatch) {
             bk = tma && r0 + kPartRound + 4 <= (long long)n + 1;
-        } else if (tma && r0 + kPartRound < (long long)n) {
-            // the round lies inside one string when the string holding its
-            // first position also holds the next round's first position (two
-            // independent loads; the string's offsets come from warp 1)
-            const long long t0 = r0 / kTile;
-            const long long j = s.tile_seg[t0], jn = s.tile_seg[t0 + kPartRound / kTile];
-            const long long l0 = r0 + j;              // the round's first lcp entry
-            lsrc = l0 & ~3LL;
-            cnt = (l0 + kPartRound + 1 - lsrc + 3) & ~3LL;
-            if (j >= 0 && j < segs.num && jn == j && lsrc >= 0 && lsrc + cnt <= (long long)n + segs.num) {
-                bk = 1;
-                shift = (int)(l0 - lsrc);
+            if (bk) {
+                mbar_init(&load_bar, 1);
+                mbar_fence_init();
+                mbar_arrive_tx(&load_bar, (unsigned)(kPartRound * 4 + cnt * 4));
+                bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
+                bulk_g2s(const_cast<int32_t*>(Slcp), lcp + lsrc, (unsigned)(cnt * 4), &load_bar);
+            }
+        } else if (tma && r0 + kPartRound <= (long long)n) {
+            sab = 1;
+            mbar_init(&load_bar, 1);
+            mbar_init(&load_bar2, 1);
+            mbar_fence_init();
+            mbar_arrive_tx(&load_bar, (unsigned)(kPartRound * 4));
+            bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
+            if (r0 + kPartRound < (long long)n) {
+                // the round lies inside one string when the string holding
+                // its first position also holds the next round's first
+                // position (two independent loads; the string's offsets come
+                // from warp 1)
+                const long long t0 = r0 / kTile;
+                const long long j = s.tile_seg[t0], jn = s.tile_seg[t0 + kPartRound / kTile];
+                const long long l0 = r0 + j;          // the round's first lcp entry
+                lsrc = l0 & ~3LL;
+                cnt = (l0 + kPartRound + 1 - lsrc + 3) & ~3LL;
+                if (j >= 0 && j < segs.num && jn == j && lsrc >= 0 && lsrc + cnt <= (long long)n + segs.num) {
+                    bk = 1;
+                    shift = (int)(l0 - lsrc);
+                    mbar_arrive_tx(&load_bar2, (unsigned)(cnt * 4));
+                    bulk_g2s(const_cast<int32_t*>(Slcp), lcp + lsrc, (unsigned)(cnt * 4), &load_bar2);
+                }
             }
         }
         bulk_s = bk;
         shift_s = shift;
-        if (bk) {
-            mbar_init(&load_bar, 1);
-            mbar_fence_init();
-            mbar_arrive_tx(&load_bar, (unsigned)(kPartRound * 4 + cnt * 4));
-            bulk_g2s(const_cast<int32_t*>(Ssa), sa + r0, kPartRound * 4, &load_bar);
-            bulk_g2s(const_cast<int32_t*>(Slcp), lcp + lsrc, (unsigned)(cnt * 4), &load_bar);
-        }
+        sab_s = sab;
     }
     if constexpr (kBatch) {
         // the string of a round that may arrive by bulk copies: its offset
@@ -420,10 +433,11 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
         }
     }
     for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
-    // a round across strings copies nothing in bulk: its string offsets use
-    // the bulk-copy area (read only before the stage area is written)
-    static_assert((kSegCap + 1) * 8 <= kPartLoadBytes, "string offsets must fit the bulk-copy area");
-    long long* seg_sh = reinterpret_cast<long long*>(smem_raw + part_load_offset(nb));
+    // a round across strings copies no lcp slice: its string offsets use
+    // the lcp part of the bulk-copy area (read only before the stage area is
+    // written)
+    static_assert((kSegCap + 1) * 8 <= kPartLcpCap * 4, "string offsets must fit the lcp copy area");
+    long long* seg_sh = reinterpret_cast<long long*>(const_cast<int32_t*>(Slcp));
     SegView sv{};
     __syncthreads();
     const bool bulk = bulk_s != 0;
@@ -446,11 +460,11 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
     uint32_t p[kPartPer];
     int32_t L[kPartPer];
     long long hint = kBatch ? sv.j0 : 0;
-    bool landed = true;
-    if (bulk && !mbar_wait(&load_bar, 0)) {           // the copies never landed: report, load nothing
-        landed = false;
-        if (threadIdx.x == 0) report(s, kErrTimeout);
-    }
+    const bool sab = kBatch ? sab_s != 0 : bulk;      // sa of the round in shared memory
+    bool landed = true;                               // false: the copies never landed (reported; load nothing)
+    if (sab && !mbar_wait(&load_bar, 0)) landed = false;
+    if (kBatch && bulk && landed && !mbar_wait(&load_bar2, 0)) landed = false;
+    if (!landed && threadIdx.x == 0) report(s, kErrTimeout);
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const long long r = r0 + (long long)j * kPartThreads + threadIdx.x;
@@ -472,7 +486,8 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             }
             L[j] = Lj;
         } else if (r < n) {
-            uint32_t pl = (uint32_t)__ldcs(sa + r);
+            if (sab && !landed) { p[j] = 0xffffffffu; L[j] = 0; continue; }
+            uint32_t pl = sab ? (uint32_t)Ssa[j * kPartThreads + (int)threadIdx.x] : (uint32_t)__ldcs(sa + r);
             long long base = 0, nj = n, lidx = r;
             if constexpr (kBatch) {
                 hint = sv.find(r, hint);
