@@ -198,12 +198,12 @@ def test_long_lengths_escape_16_bits(ctx):
 
 
 @pytest.mark.parametrize("name", ["dna_64m", "english_256m"])
-def test_full_size_exact(ctx, name):
+def test_full_size_exact(ctx, name, tmp_path):
     """Every position of the full-size workloads (64 Mi planted-repeat DNA,
     256 Mi english) against Algorithm 3, run on all host cores over disjoint
     blocks of positions: the all-LR query with both front ends, the
     leftmost-only query and the raw-LLR variant; plus the size-independent
-    properties."""
+    properties, and the autotuner's other kernel shapes."""
     w = W.single(name)
     got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa")
     want = oracle.lr_at_range(w.rank, w.lcp, 0, w.n, threads=os.cpu_count() or 1)
@@ -220,6 +220,22 @@ def test_full_size_exact(ctx, name):
     got2 = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
     for a, b in zip(got, got2):
         assert np.array_equal(a, b)
+    del got2
+    # the other shapes the autotuner can pick at this size (warp-segment
+    # cover; tile cover with 2048- or 8192-position tiles; the warp-segment
+    # cover behind the rank gather), forced through an autotune table
+    lg = w.n.bit_length() - 1
+    for code in (0, 8, 12, 2):
+        path = tmp_path / ("codes%d.txt" % code)
+        path.write_text("%d %d\n" % (lg * 64 + lg, code))
+        c = P.Context(0)
+        try:
+            P.lr_autotune_load(c.handle, str(path))
+            got3 = tuple(t.cpu().numpy() for t in c.query_all(_dev(w.lcp), sa=_dev(w.sa), rank=_dev(w.rank)))
+        finally:
+            c.close()
+        _assert_csr_equal(got3, got, "%s, shape code %d" % (name, code))
+        del got3
 
 
 def test_513_super_buckets(ctx):
