@@ -74,7 +74,7 @@ lr_status cuda_fail(lr_ctx* ctx, cudaError_t e) {
 }
 
 struct Layout {
-    size_t off_status_g, off_status_b, off_status_o, off_status_w, off_cursor1, off_cursor2, zero_end;
+    size_t off_status_g, off_status_b, off_status_o, off_status_w, off_cursor1, off_cursor2, off_cursor_w, zero_end;
     size_t off_tile_cbase, off_seg_cbase, off_tile_seg, off_cstart, off_cend, off_ent1, off_ent2, off_lbig, off_halo,
         total;
 };
@@ -88,7 +88,8 @@ Layout layout_for(long long n) {
     L.off_status_w = align_up(L.off_status_o + (size_t)nt * 8);
     L.off_cursor1 = align_up(L.off_status_w + (size_t)lr::num_seg_tiles(n) * 8);
     L.off_cursor2 = align_up(L.off_cursor1 + (size_t)ns * 4 * lr::kCursorStride);
-    L.zero_end = L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride;
+    L.off_cursor_w = align_up(L.off_cursor2 + (size_t)nb * 4 * lr::kCursorStride);
+    L.zero_end = L.off_cursor_w + (size_t)lr::num_wins(n) * 4 * lr::kCursorStride;
     L.off_tile_cbase = align_up(L.zero_end);
     L.off_seg_cbase = align_up(L.off_tile_cbase + (size_t)(nt + 1) * 4);
     L.off_tile_seg = align_up(L.off_seg_cbase + (size_t)(ng + 1) * 4);
@@ -116,6 +117,8 @@ void carve(unsigned char* b, long long cap_n, long long n, unsigned* d_err, lr::
     s->seg_cbase = (int32_t*)(b + L.off_seg_cbase);
     s->cursor1 = (unsigned*)(b + L.off_cursor1);
     s->cursor2 = (unsigned*)(b + L.off_cursor2);
+    s->cursor_w = (unsigned*)(b + L.off_cursor_w);
+    s->went = (unsigned long long*)(b + L.off_cstart);     // cstart + cend: 8 bytes per position
     s->tile_cbase = (int32_t*)(b + L.off_tile_cbase);
     s->tile_seg = (int32_t*)(b + L.off_tile_seg);
     s->cstart = (int32_t*)(b + L.off_cstart);
@@ -128,6 +131,7 @@ void carve(unsigned char* b, long long cap_n, long long n, unsigned* d_err, lr::
     s->nsegs = lr::num_segs(n);
     s->nbuckets = lr::num_buckets(n);
     s->nsupers = lr::num_supers(n);
+    s->nwins = lr::num_wins(n);
     s->zero_base = b;
     s->zero_bytes = L.zero_end;          // covers the status words and cursors of any n <= cap_n
 }

@@ -352,14 +352,85 @@ __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned
     else part_reserve_r<4>(p, nb, cursor);
 }
 
-// Level 1: Lemma 1 in rank order, then the partition of the packed entries
-// <position mod 2^20, min(L, 4095)> into super-buckets of 2^20 positions.
-// Each CTA takes kPartRound consecutive ranks, counts them per super-bucket
-// in shared memory, reserves room with one global atomic per touched
-// super-bucket (cursors one cache line apart) and writes its entries in
-// bucket order.  A length of 4095 or more is stored in lbig (field 4095);
-// the length of the last position of every bucket goes to halo (the next
-// bucket's predecessor).
+// Slot of this lane's entry in bucket b among the entries counted so far,
+// with one shared atomic per run of lanes (in lane order) that carry the
+// same b: entries that arrive clustered by bucket would otherwise serialise
+// on one counter.  All lanes of the warp call it; a lane with !valid gets
+// no slot (and b is ignored).
+__device__ __forceinline__ uint32_t run_slot(uint32_t* hist, uint32_t b, bool valid) {
+    const int lane = lane_id();
+    const uint32_t bk = valid ? b : 0xffffffffu;
+    const uint32_t pb = __shfl_up_sync(kFull, bk, 1);
+    const bool head = lane == 0 || bk != pb;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned upto = (2u << lane) - 1u;           // lanes 0 .. lane
+    const int h = 31 - __clz(heads & upto);            // head of this lane's run
+    const unsigned after = heads & ~upto;
+    const int next = after ? __ffs(after) - 1 : kWarp; // head of the next run
+    uint32_t base = 0;
+    if (head && valid) base = atomicAdd(hist + b, (uint32_t)(next - lane));
+    base = __shfl_sync(kFull, base, h);
+    return base + (uint32_t)(lane - h);
+}
+
+// The level-1 partition of one round's <position p[j], length L[j]> pairs
+// (entry j of each thread, at round index j * kPartThreads + thread, when
+// that index is below cnt): counted per super-bucket in
+// shared memory, room reserved with one global atomic per touched
+// super-bucket (cursors one cache line apart), staged in bucket order and
+// written out as <position mod 2^20, min(L, 4095)>.  A length of 4095 or
+// more is stored in lbig (field 4095); the length of the last position of
+// every bucket goes to halo (the next bucket's predecessor).  Returns 1
+// after an input error (a position out of range, or more than 2^20 of them
+// in a super-bucket: the positions are not a permutation).
+__device__ __forceinline__ unsigned level1_scatter(const PartSmem& P, int nb, const Scratch& s, int32_t n,
+                                                   const uint32_t (&p)[kPartPer], const int32_t (&L)[kPartPer],
+                                                   int cnt) {
+    unsigned bad = 0;
+    uint32_t ent[kPartPer], key[kPartPer];          // key: bucket << 16 | slot, or ~0u
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const bool in = j * kPartThreads + (int)threadIdx.x < cnt;
+        const uint32_t pj = p[j];
+        const bool ok = in && pj < (uint32_t)n;
+        if (in && !ok) bad = 1;
+        uint32_t b1 = 0;
+        if (ok) {
+            const int32_t Lj = L[j];
+            uint32_t field = (uint32_t)Lj;
+            if (field >= kEsc12) { field = kEsc12; s.lbig[pj] = Lj; }
+            if ((pj & (kBucket - 1)) == kBucket - 1) s.halo[(pj >> kBucketLog) + 1] = Lj;
+            b1 = pj >> kSuperLog;
+            ent[j] = ((pj & (kSuper - 1)) << 12) | field;
+        }
+        const uint32_t slot = run_slot(P.hist, b1, ok);     // the pairs come in runs of one super-bucket
+        key[j] = ok ? ((b1 << 16) | slot) : 0xffffffffu;
+    }
+    __syncthreads();
+    part_reserve(P, nb, s.cursor1);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        if (key[j] == 0xffffffffu) continue;
+        const uint32_t b1 = key[j] >> 16;
+        const uint32_t o = P.loff[b1] + (key[j] & 0xffffu);
+        P.stage[o] = ent[j];
+        P.sbk[o] = (uint16_t)b1;
+    }
+    __syncthreads();
+    const uint32_t total = P.loff[nb];
+    for (uint32_t i = threadIdx.x; i < total; i += kPartThreads) {
+        const uint32_t b1 = P.sbk[i];
+        const uint32_t idx = P.base[b1] + (i - P.loff[b1]);
+        if (idx < (uint32_t)kSuper) s.ent1[((size_t)b1 << kSuperLog) + idx] = P.stage[i];
+        else bad = 1;
+    }
+    return bad;
+}
+
+// Level 1: Lemma 1 in rank order.  Each CTA takes kPartRound consecutive
+// ranks r, forms <sa[r], max(lcp[r], lcp[r+1])> and partitions these pairs
+// into super-buckets of 2^20 positions (level1_scatter).
 template <bool kBatch>
 __global__ void __launch_bounds__(kPartThreads, kPartBlocks)
 k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t n, Scratch s, Segs segs, int tma) {
@@ -509,6 +580,8 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             p[j] = 0xffffffffu; L[j] = 0;
         }
     }
+    // the steps of level1_scatter, kept inline here (as a call they cost this
+    // kernel 3 %: more register spills)
     uint32_t ent[kPartPer], key[kPartPer];          // key: bucket << 16 | slot, or ~0u
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
@@ -547,9 +620,124 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
     if (bad) report(s, kErrInput);
 }
 
+// Rank-window front end (rank without sa, one string of 2^24 positions or
+// more).  Lemma 1 in text order, max(lcp[rank[i]], lcp[rank[i] + 1]), makes
+// k_gather_llr read one random lcp sector per position from HBM.  Here
+// k_rank_win first partitions the pairs <rank[i], i> by rank into windows
+// of 2^22 ranks (8-byte entries rank << 32 | i, in the compact LLR region,
+// which is idle until k_bucket_llr).  k_part1_win then takes kPartRound
+// pairs of one window per CTA, gathers their two lcp words from the
+// window's 16 MB slice of lcp (CTAs run in window order, so the slice stays
+// in L2 while its window is processed) and partitions <i, L_i> into the
+// level-1 super-buckets like k_part1.  k_part2 and k_bucket_llr follow
+// unchanged.
+__host__ __device__ inline size_t win_stage_offset(int nw) { return ((size_t)(2 * nw + 1) * 4 + 15) & ~(size_t)15; }
+size_t rank_win_smem_bytes(int nw) { return win_stage_offset(nw) + (size_t)kPartRound * 10; }
+size_t part_scatter_smem_bytes(int nb) { return (size_t)(2 * nb + 1) * 4 + (size_t)kPartRound * 6; }
+
+__global__ void __launch_bounds__(kPartThreads, kPartBlocks)
+k_rank_win(const int32_t* __restrict__ rank, int32_t n, Scratch s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nw = (int)s.nwins;                      // <= kMaxWins
+    const PartSmem P = part_smem(smem_raw, nw);       // counters; the stage area is the 8-byte one below
+    unsigned long long* stage = reinterpret_cast<unsigned long long*>(smem_raw + win_stage_offset(nw));
+    uint16_t* sbk = reinterpret_cast<uint16_t*>(stage + kPartRound);
+    const long long i0 = (long long)blockIdx.x * kPartRound;
+    for (int b = threadIdx.x; b < nw; b += kPartThreads) P.hist[b] = 0;
+    __syncthreads();
+    unsigned bad = 0;
+    uint32_t rk[kPartPer], key[kPartPer];             // key: window << 16 | slot, or ~0u
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const long long i = i0 + (long long)j * kPartThreads + threadIdx.x;
+        key[j] = 0xffffffffu;
+        rk[j] = 0;
+        if (i >= n) continue;
+        const uint32_t r = (uint32_t)__ldcs(rank + i);
+        if (r >= (uint32_t)n) { bad = 1; continue; }
+        const uint32_t w = r >> kWinLog;
+        rk[j] = r;
+        key[j] = (w << 16) | atomicAdd(&P.hist[w], 1u);
+    }
+    __syncthreads();
+    part_reserve(P, nw, s.cursor_w);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        if (key[j] == 0xffffffffu) continue;
+        const uint32_t w = key[j] >> 16;
+        const uint32_t o = P.loff[w] + (key[j] & 0xffffu);
+        stage[o] = ((unsigned long long)rk[j] << 32) | (uint32_t)(i0 + j * kPartThreads + threadIdx.x);
+        sbk[o] = (uint16_t)w;
+    }
+    __syncthreads();
+    const uint32_t total = P.loff[nw];
+    for (uint32_t t = threadIdx.x; t < total; t += kPartThreads) {
+        const uint32_t w = sbk[t];
+        const uint32_t slot = P.base[w] + (t - P.loff[w]);
+        const long long idx = ((long long)w << kWinLog) + slot;
+        if (slot < (1u << kWinLog) && idx < n) s.went[idx] = stage[t];
+        else bad = 1;                                 // a window overflows: rank is not a permutation
+    }
+    if (bad) report(s, kErrInput);
+}
+
+__global__ void __launch_bounds__(kPartThreads, kPartBlocks)
+k_part1_win(const int32_t* __restrict__ lcp, int32_t n, Scratch s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = (int)s.nsupers;
+    const PartSmem P = part_smem(smem_raw, nb);
+    constexpr int kRoundsPerWin = (1 << kWinLog) / kPartRound;
+    const long long w = blockIdx.x / kRoundsPerWin;
+    const int q = blockIdx.x % kRoundsPerWin;
+    const uint32_t fill = __ldcg(s.cursor_w + (size_t)w * kCursorStride);
+    const long long wsize = ((long long)n - (w << kWinLog) < (1LL << kWinLog)) ? (long long)n - (w << kWinLog)
+                                                                                : (1LL << kWinLog);
+    for (int b = threadIdx.x; b < nb; b += kPartThreads) P.hist[b] = 0;
+    unsigned bad = 0;
+    if (q == 0 && threadIdx.x == 0) {
+        if ((long long)fill != wsize) bad = 1;                  // rank is not a permutation
+        if (w == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;   // lcp sentinels
+    }
+    __syncthreads();
+    const long long lim = (long long)fill < wsize ? (long long)fill : wsize;
+    const long long e0 = (long long)q * kPartRound;
+    if (e0 >= lim) {                                  // uniform over the CTA
+        if (bad) report(s, kErrInput);
+        return;
+    }
+    const int cnt = (int)(lim - e0 < kPartRound ? lim - e0 : kPartRound);
+    const unsigned long long* src = s.went + (w << kWinLog) + e0;
+    uint32_t p[kPartPer];
+    int32_t L[kPartPer];
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {              // all pairs in flight first: p = i, L = rank
+        const int x = j * kPartThreads + (int)threadIdx.x;
+        const unsigned long long e = (x < cnt) ? __ldcs(src + x) : 0xffffffffull;
+        p[j] = (uint32_t)e;
+        L[j] = (int32_t)(e >> 32);
+    }
+#pragma unroll
+    for (int j = 0; j < kPartPer; ++j) {
+        const int x = j * kPartThreads + (int)threadIdx.x;
+        if (x >= cnt) continue;
+        const uint32_t i = p[j], r = (uint32_t)L[j];
+        if (i >= (uint32_t)n || r >= (uint32_t)n) { bad = 1; p[j] = 0xffffffffu; L[j] = 0; continue; }
+        const int32_t a = __ldg(lcp + r), c = __ldg(lcp + r + 1);
+        int32_t Lj = a > c ? a : c;
+        if (Lj < 0 || (long long)Lj > (long long)n - i) { bad = 1; Lj = 0; }
+        L[j] = Lj;
+    }
+    bad |= level1_scatter(P, nb, s, n, p, L, cnt);
+    if (bad) report(s, kErrInput);
+}
+
 // Level 2: each CTA takes kPartRound entries of one super-bucket and splits
 // them into its kSubPerSuper buckets, entries <position mod 2^15, field>
 // (field = L, or kEsc17 when L is in lbig), the same way as level 1.
+// kRuns: slots by run_slot, for level-1 entries that come clustered by
+// bucket (those of the rank-window front end).
+template <bool kRuns>
 __global__ void __launch_bounds__(kPartThreads, kPartBlocks)
 k_part2(int32_t n, Scratch s) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -576,12 +764,24 @@ k_part2(int32_t n, Scratch s) {
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const uint32_t i = i0 + j * kPartThreads + threadIdx.x;
-        key[j] = 0xffffffffu;
-        if (i >= fill) continue;
-        const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
-        const uint32_t b2 = low20 >> kBucketLog;
-        ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
-        key[j] = (b2 << 16) | atomicAdd(&P.hist[b2], 1u);
+        if constexpr (kRuns) {
+            const bool ok = i < fill;
+            uint32_t b2 = 0;
+            if (ok) {
+                const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
+                b2 = low20 >> kBucketLog;
+                ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
+            }
+            const uint32_t slot = run_slot(P.hist, b2, ok);
+            key[j] = ok ? ((b2 << 16) | slot) : 0xffffffffu;
+        } else {
+            key[j] = 0xffffffffu;
+            if (i >= fill) continue;
+            const uint32_t low20 = ent[j] >> 12, f12 = ent[j] & kEsc12;
+            const uint32_t b2 = low20 >> kBucketLog;
+            ent[j] = ((low20 & (kBucket - 1)) << 17) | (f12 == kEsc12 ? kEsc17 : f12);
+            key[j] = (b2 << 16) | atomicAdd(&P.hist[b2], 1u);
+        }
     }
     __syncthreads();
     const long long bb = b1 * kSubPerSuper;
@@ -751,7 +951,17 @@ void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Sc
     else
         k_part1<false><<<g1, kPartThreads, part_smem_bytes((int)s.nsupers), stream>>>(sa, lcp, n, s, segs, tma);
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
-    k_part2<<<g2, kPartThreads, part2_smem_bytes(), stream>>>(n, s);
+    k_part2<false><<<g2, kPartThreads, part2_smem_bytes(), stream>>>(n, s);
+}
+
+void launch_rank_window_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
+                              cudaStream_t stream) {
+    const unsigned g0 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
+    k_rank_win<<<g0, kPartThreads, rank_win_smem_bytes((int)s.nwins), stream>>>(rank, n, s);
+    const unsigned g1 = (unsigned)(s.nwins * ((1 << kWinLog) / kPartRound));
+    k_part1_win<<<g1, kPartThreads, part_scatter_smem_bytes((int)s.nsupers), stream>>>(lcp, n, s);
+    const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
+    k_part2<true><<<g2, kPartThreads, part2_smem_bytes(), stream>>>(n, s);
 }
 
 void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream) {
@@ -766,7 +976,14 @@ cudaError_t configure_front() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_part1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem_bytes(2048));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_part2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_rank_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rank_win_smem_bytes(kMaxWins));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_part1_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)part_scatter_smem_bytes(2048));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_part2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part2_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_part2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)part2_smem_bytes());
 }
 

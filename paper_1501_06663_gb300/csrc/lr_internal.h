@@ -32,6 +32,13 @@ constexpr int kPartRound = kPartThreads * kPartPer;   // 4096 entries per partit
 constexpr uint32_t kEsc12 = 0xfffu;            // 12-bit length field of level 1: value in lbig
 constexpr uint32_t kEsc17 = 0x1ffffu;          // 17-bit length field of level 2: value in lbig
 constexpr int kCursorStride = 32;              // one 128-byte line per partition cursor
+// Rank-window front end (rank without sa, one string): the pairs
+// <rank[i], i> partitioned by rank into windows of 2^22 ranks, so that the
+// lcp words of a window (16 MB) are gathered from L2.  Used from n = 2^24 on
+// (below that, all of lcp fits in L2 and the plain gather is as good).
+constexpr int kWinLog = 22;
+constexpr int kMaxWins = 512;                  // n < 2^31
+constexpr long long kRankWinMinN = 1LL << 24;
 
 // Polls of a look-back status word before the wait is declared lost (a
 // few seconds at most; the kernel then reports kErrTimeout and finishes).
@@ -63,6 +70,10 @@ struct Scratch {
     long long nsupers;
     void* zero_base;               // tickets, status words and cursors, cleared before every query
     size_t zero_bytes;
+    unsigned* cursor_w = nullptr;  // fill counts of the rank windows, one per kCursorStride words (cleared
+                                   // per query); null where the scratch has no room for the rank-window front
+    unsigned long long* went = nullptr;   // n: rank-window entries rank << 32 | i (in the cstart / cend region)
+    long long nwins = 0;
     int spin_limit = kSpinLimit;   // polls of one look-back wait before it gives up
     long long hold_tile = -1;      // test hook: this cover tile never publishes its look-back word
 };
@@ -75,6 +86,7 @@ __host__ __device__ inline long long num_segs(long long n) { return (n + kSeg - 
 __host__ __device__ inline long long num_seg_tiles(long long n) { return (n + kSegTile - 1) / kSegTile; }
 inline long long num_buckets(long long n) { return (n + kBucket - 1) / kBucket; }
 inline long long num_supers(long long n) { return (n + kSuper - 1) / kSuper; }
+inline long long num_wins(long long n) { return (n + (1LL << kWinLog) - 1) >> kWinLog; }
 
 constexpr int kMaxPhases = 8;
 
@@ -115,6 +127,9 @@ void launch_gather_front(const int32_t* rank, const int32_t* lcp, int32_t n, con
 void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Scratch& s, const Segs& segs,
                       cudaStream_t stream);
 void launch_bucket_front(int32_t n, const Scratch& s, cudaStream_t stream);
+// k_rank_win, k_part1_win and k_part2 (the rank-window front end up to the bucket kernel)
+void launch_rank_window_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
+                              cudaStream_t stream);
 void launch_cover(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,
                   int32_t* starts, long long capacity, bool all, int tiles_per, cudaStream_t stream);
 void launch_cover_w(int32_t n, const Scratch& s, int32_t* lr_len, int32_t* lr_start, int64_t* offsets,

@@ -35,7 +35,7 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-FRONTS = ("sa", "rank")        # rank-order front end (suffix array given) and the rank gather
+FRONTS = ("sa", "rank")        # rank-order front end (suffix array given); rank alone (rank gather, or rank windows from 2^24 positions on)
 
 
 def _gpu_all(ctx, sa, rank, lcp, front="sa"):
@@ -242,7 +242,7 @@ def test_513_super_buckets(ctx):
     """n = 2^29 + 12345 planted-repeat DNA: the first partition level spreads
     the rank-order entries over 513 super-buckets of 2^20 positions, the last
     of them (and its last bucket of 2^15) ragged.  Every position against
-    Algorithm 3."""
+    Algorithm 3, then the rank-window front end against that result."""
     n = (1 << 29) + 12345
     free, _ = torch.cuda.mem_get_info()
     if free < n * 64:
@@ -253,6 +253,9 @@ def test_513_super_buckets(ctx):
     got = _gpu_all(ctx, sa, rank, lcp, "sa")
     want = oracle.lr_at_range(rank, lcp, 0, n, threads=os.cpu_count() or 1)
     _assert_csr_equal(got, want, "n = 2^29 + 12345")
+    del want
+    # rank alone: the rank-window front end over 129 windows of 2^22 ranks, the last ragged
+    _assert_csr_equal(_gpu_all(ctx, sa, rank, lcp, "rank"), got, "n = 2^29 + 12345, rank windows")
 
 
 # ------------------------------------------------------------------ API behaviour
@@ -325,6 +328,29 @@ def test_bad_sentinel_and_rank_are_reported(ctx):
     # the context stays usable
     for front in FRONTS:
         _assert_csr_equal(_gpu_all(ctx, w.sa, w.rank, w.lcp, front), oracle.lr_all_raw(w.rank, w.lcp))
+
+
+def test_bad_rank_in_the_rank_window_front(ctx):
+    """Rank alone for one string of 2^24 positions or more goes through the
+    rank-window front end; a rank that is out of range, a rank given twice
+    and a broken lcp sentinel are reported there, and the context stays
+    usable."""
+    w = W.single("english_256m", n=(1 << 24) + 5)
+    for what in ("range", "twice", "sentinel"):
+        rank, lcp = w.rank.copy(), w.lcp
+        if what == "range":
+            rank[17] = w.n + 100
+        elif what == "twice":
+            rank[17] = rank[(1 << 23) + 3]
+        else:
+            lcp = w.lcp.copy()
+            lcp[w.n] = 2
+        with pytest.raises(P.LRError) as e:
+            ctx.query_all(_dev(lcp), rank=_dev(rank))
+        assert e.value.status == P.LR_ERR_SENTINEL, what
+    got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
+    _assert_csr_equal(got, _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa"), "after the errors")
+    _sampled_check(ctx, w, got, 200, 23)
 
 
 def test_maximum_size_closed_form(ctx):
