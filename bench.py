@@ -612,7 +612,8 @@ def run_ours(args):
         return [a / reps for a in acc]
 
     per = phase_avg()
-    # the paper's own data flow (rank + random lcp gather), same cover kernel, for comparison
+    # rank alone (the paper's inputs): the rank-window front end from 2^24
+    # positions on, else the rank gather; same cover kernel
     for _ in range(2):
         step(sa=None, rank=d_rank)
     torch.cuda.synchronize(dev)
@@ -626,6 +627,28 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     gather_ms = g0.elapsed_time(g1) / gsteps
     per_gather = phase_avg(sa=None, rank=d_rank)
+    rank_front = "rank windows" if len(per_gather) == 3 else "rank gather"
+    rank_names = ["rank_windows_partition", "bucket_llr", "cover"] if len(per_gather) == 3 else ["gather_llr", "cover"]
+    # the paper's data flow itself (rank + a random gather of lcp), run as a
+    # batch of one string, which always takes the gather
+    paper_gather = None
+    if rank_front == "rank windows":
+        d_off1 = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        desc1 = lr.batch_desc(d_off1, d_lcp, rank=d_rank)
+
+        def gather_step():
+            r, _ = lr.lr_batch_query_all(ctx, desc1, ln, st, off, starts, stream, sync=False)
+            if r != lr.LR_OK:
+                raise lr.LRError(r, "lr_batch_query_all (rank gather)")
+
+        pg_ms = _event_ms(stream, gather_step, max(3, min(args.steps, 10)), warm=2)
+        lr.lr_set_phase_timing(ctx, True)
+        gather_step()
+        pg = lr.lr_phase_times(ctx)
+        lr.lr_set_phase_timing(ctx, False)
+        paper_gather = {"ms_per_step": round(pg_ms, 4), "value": round(whole_job_rate(ws, n, pg_ms), 3),
+                        "kernel_ms": {nm: round(t, 4) for nm, t in zip(["gather_llr", "cover"], pg)},
+                        "how": "one-string batch (lr_batch_query_all), rank only"}
 
     # the leftmost-only query (Algorithm 2's output, no CSR pass), same front end
     def leftmost():
@@ -803,10 +826,10 @@ def run_ours(args):
             "raw_llr_variant": raw,
             "index_build": index_build,
             "leftmost_query": leftmost_query,
-            "rank_gather_front": {"ms_per_step": round(gather_ms, 4),
-                                  "value": round(whole_job_rate(ws, n, gather_ms), 3),
-                                  "kernel_ms": {nm: round(p, 4) for nm, p in
-                                                zip(["gather_llr", "cover"], per_gather)}},
+            "rank_only_query": {"ms_per_step": round(gather_ms, 4),
+                                "value": round(whole_job_rate(ws, n, gather_ms), 3), "front": rank_front,
+                                "kernel_ms": {nm: round(p, 4) for nm, p in zip(rank_names, per_gather)}},
+            "rank_gather_front": paper_gather,
             "cpu_baseline": {"value": round(rate, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "Algorithm 3 (two leftward raw-LLR walks per position) on positions "
                                        "[%d, %d) of the same workload, split into %d blocks run at once on the "
