@@ -636,24 +636,40 @@ size_t rank_win_smem_bytes(int nw) { return win_stage_offset(nw) + (size_t)kPart
 size_t part_scatter_smem_bytes(int nb) { return (size_t)(2 * nb + 1) * 4 + (size_t)kPartRound * 6; }
 
 __global__ void __launch_bounds__(kPartThreads, kPartBlocks)
-k_rank_win(const int32_t* __restrict__ rank, int32_t n, Scratch s) {
+k_rank_win(const int32_t* __restrict__ rank, int32_t n, Scratch s, int tma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long load_bar;
     const int nw = (int)s.nwins;                      // <= kMaxWins
     const PartSmem P = part_smem(smem_raw, nw);       // counters; the stage area is the 8-byte one below
     unsigned long long* stage = reinterpret_cast<unsigned long long*>(smem_raw + win_stage_offset(nw));
     uint16_t* sbk = reinterpret_cast<uint16_t*>(stage + kPartRound);
+    // a full round's ranks arrive by one bulk copy into the stage area,
+    // which is written only after every thread has read its ranks
+    const int32_t* Srk = reinterpret_cast<const int32_t*>(stage);
     const long long i0 = (long long)blockIdx.x * kPartRound;
+    const bool bulk = tma && i0 + kPartRound <= (long long)n;
+    if (threadIdx.x == 0 && bulk) {
+        mbar_init(&load_bar, 1);
+        mbar_fence_init();
+        mbar_arrive_tx(&load_bar, (unsigned)(kPartRound * 4));
+        bulk_g2s(const_cast<int32_t*>(Srk), rank + i0, kPartRound * 4, &load_bar);
+    }
     for (int b = threadIdx.x; b < nw; b += kPartThreads) P.hist[b] = 0;
     __syncthreads();
     unsigned bad = 0;
+    bool landed = true;                               // false: the copy never landed (reported; load nothing)
+    if (bulk && !mbar_wait(&load_bar, 0)) {
+        landed = false;
+        if (threadIdx.x == 0) report(s, kErrTimeout);
+    }
     uint32_t rk[kPartPer], key[kPartPer];             // key: window << 16 | slot, or ~0u
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         const long long i = i0 + (long long)j * kPartThreads + threadIdx.x;
         key[j] = 0xffffffffu;
         rk[j] = 0;
-        if (i >= n) continue;
-        const uint32_t r = (uint32_t)__ldcs(rank + i);
+        if (i >= n || !landed) continue;
+        const uint32_t r = bulk ? (uint32_t)Srk[j * kPartThreads + threadIdx.x] : (uint32_t)__ldcs(rank + i);
         if (r >= (uint32_t)n) { bad = 1; continue; }
         const uint32_t w = r >> kWinLog;
         rk[j] = r;
@@ -957,7 +973,8 @@ void launch_partition(const int32_t* sa, const int32_t* lcp, int32_t n, const Sc
 void launch_rank_window_front(const int32_t* rank, const int32_t* lcp, int32_t n, const Scratch& s,
                               cudaStream_t stream) {
     const unsigned g0 = (unsigned)(((long long)n + kPartRound - 1) / kPartRound);
-    k_rank_win<<<g0, kPartThreads, rank_win_smem_bytes((int)s.nwins), stream>>>(rank, n, s);
+    const int tma = ((uintptr_t)rank & 15u) == 0 ? 1 : 0;   // bulk copies need a 16-byte-aligned source
+    k_rank_win<<<g0, kPartThreads, rank_win_smem_bytes((int)s.nwins), stream>>>(rank, n, s, tma);
     const unsigned g1 = (unsigned)(s.nwins * ((1 << kWinLog) / kPartRound));
     k_part1_win<<<g1, kPartThreads, part_scatter_smem_bytes((int)s.nsupers), stream>>>(lcp, n, s);
     const unsigned g2 = (unsigned)(s.nsupers * (kSuper / kPartRound));
