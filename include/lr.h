@@ -22,8 +22,12 @@
  *   - with sa, the lengths are computed in rank order (sa and lcp read
  *     once, coalesced) and radix-partitioned back to text order;
  *   - with rank only, each position gathers its two lcp words, the paper's
- *     own data flow (Sec. 4): one random 32-byte sector per position.
- * Both give identical results.  sa must be a permutation of [0, n) and rank
+ *     own data flow (Sec. 4): one random 32-byte sector per position.  For
+ *     one string of 2^24 positions or more (not a batch, not the static
+ *     call), the pairs <rank[i], i> are first partitioned into windows of
+ *     2^22 ranks, so that each window's gathers hit L2, and then join the
+ *     sa path's partition.
+ * All give identical results.  sa must be a permutation of [0, n) and rank
  * its inverse; a violation that the kernels detect is reported as
  * LR_ERR_SENTINEL, and no input ever makes a kernel access memory out of
  * bounds.
@@ -248,7 +252,8 @@ lr_status lr_batch_query_all(lr_ctx* ctx, lr_stream_t stream, const lr_batch_des
  * rank-order front end (code 9).  *choice receives the chosen shape code: bit 3 clear: the
  * warp-segment cover (bits 0 and 2 clear); bit 3 set: the tile cover, with
  * bit 0: 4096-position tiles, bit 2: 8192-position tiles, neither: 2048;
- * bit 1: the rank-gather front end.  The outputs are overwritten.
+ * bit 1: the rank front end (timed as the rank gather; a single query of
+ * 2^24 positions or more with this code takes the rank windows).  The outputs are overwritten.
  * lr_autotune_save / _load write and read the remembered choices as a small
  * text file (one "class code" pair per line; invalid codes are skipped).
  */
