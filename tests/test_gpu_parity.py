@@ -351,6 +351,9 @@ def test_bad_rank_in_the_rank_window_front(ctx):
     got = _gpu_all(ctx, w.sa, w.rank, w.lcp, "rank")
     _assert_csr_equal(got, _gpu_all(ctx, w.sa, w.rank, w.lcp, "sa"), "after the errors")
     _sampled_check(ctx, w, got, 200, 23)
+    # the leftmost-only query through the same front end
+    st, ln = ctx.query_leftmost(_dev(w.lcp), rank=_dev(w.rank))
+    assert np.array_equal(ln.cpu().numpy(), got[0]) and np.array_equal(st.cpu().numpy(), got[1])
 
 
 def test_maximum_size_closed_form(ctx):
