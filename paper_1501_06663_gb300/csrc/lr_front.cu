@@ -375,10 +375,12 @@ __device__ __forceinline__ uint32_t run_slot(uint32_t* hist, uint32_t b, bool va
 
 // The level-1 partition of one round's <position p[j], length L[j]> pairs
 // (entry j of each thread, at round index j * kPartThreads + thread, when
-// that index is below cnt): counted per super-bucket in
-// shared memory, room reserved with one global atomic per touched
-// super-bucket (cursors one cache line apart), staged in bucket order and
-// written out as <position mod 2^20, min(L, 4095)>.  A length of 4095 or
+// that index is below cnt), as k_part1 does it for its rank-order pairs,
+// for the rank-window front end: counted per super-bucket in shared memory
+// (one atomic per run of lanes with the same super-bucket, run_slot: the
+// rank-window pairs come in such runs), room reserved with one global
+// atomic per touched super-bucket (cursors one cache line apart), staged in
+// bucket order and written out as <position mod 2^20, min(L, 4095)>.  A length of 4095 or
 // more is stored in lbig (field 4095); the length of the last position of
 // every bucket goes to halo (the next bucket's predecessor).  Returns 1
 // after an input error (a position out of range, or more than 2^20 of them
