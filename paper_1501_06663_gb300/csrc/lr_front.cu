@@ -170,15 +170,22 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
         if (!kBatch && tile == 0 && (__ldg(lcp) != 0 || __ldg(lcp + n) != 0)) bad = 1;
     }
     hint = kBatch ? sv.j0 : 0;
+    // All rank loads, then all lcp loads, then the lengths: every load of a
+    // thread is in flight before the first one is used.  A batch tile that
+    // lies inside one string does the same with that string's offsets and
+    // checks; other batch tiles look each position's string up.
+    long long sbase = 0, snj = n, slbase = 0;
+    bool direct = true;
     if constexpr (kBatch) {
-#pragma unroll
-        for (int j = 0; j < kTile / kThreads; ++j) {
-            const int x = j * kThreads + tid;
-            Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
-        }
-    } else {
-        // all rank loads, then all lcp loads, then the lengths: every load
-        // of a thread is in flight before the first one is used
+        const long long g1 = (k0 + kTile < n) ? k0 + kTile : n;
+        const long long jk = sv.find(k0, sv.j0);
+        const long long b0 = sv.at(jk), b1 = sv.at(jk + 1);
+        direct = b0 >= 0 && b0 <= k0 && g1 <= b1 && b1 <= (long long)n;
+        sbase = b0;
+        snj = b1 - b0;
+        slbase = b0 + jk;
+    }
+    if (direct) {
         constexpr int kPer = kTile / kThreads;
         uint32_t r[kPer];
         int32_t a[kPer], c[kPer];
@@ -190,17 +197,26 @@ k_gather_llr(const int32_t* __restrict__ rank, const int32_t* __restrict__ lcp, 
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const long long k = k0 + j * kThreads + tid;
-            if (k < n && r[j] >= (uint32_t)n) { bad = 1; r[j] = 0; }
-            a[j] = (k < n) ? __ldg(lcp + r[j]) : 0;
-            c[j] = (k < n) ? __ldg(lcp + r[j] + 1) : 0;
+            if (k < n && (long long)r[j] >= snj) { bad = 1; r[j] = 0; }
+            a[j] = (k < n) ? __ldg(lcp + slbase + r[j]) : 0;
+            c[j] = (k < n) ? __ldg(lcp + slbase + r[j] + 1) : 0;
         }
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const int x = j * kThreads + tid;
             const long long k = k0 + x;
             int32_t L = a[j] > c[j] ? a[j] : c[j];
-            if (k < n && (L < 0 || (long long)L > (long long)n - k)) { bad = 1; L = 0; }
+            if (k < n) {
+                if (kBatch && ((r[j] == 0 && a[j] != 0) || ((long long)r[j] == snj - 1 && c[j] != 0))) bad = 1;
+                if (L < 0 || (long long)L > snj - (k - sbase)) { bad = 1; L = 0; }
+            }
             Ls[1 + x] = (k < n) ? L : 0;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kTile / kThreads; ++j) {
+            const int x = j * kThreads + tid;
+            Ls[1 + x] = (k0 + x < n) ? llr(k0 + x) : 0;
         }
     }
     if (bad) report(s, kErrInput);
