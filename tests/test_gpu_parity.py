@@ -354,6 +354,12 @@ def test_bad_rank_in_the_rank_window_front(ctx):
     # the leftmost-only query through the same front end
     st, ln = ctx.query_leftmost(_dev(w.lcp), rank=_dev(w.rank))
     assert np.array_equal(ln.cpu().numpy(), got[0]) and np.array_equal(st.cpu().numpy(), got[1])
+    # and the host-buffer entry point with rank alone
+    n = w.n
+    h = (np.empty(n, np.int32), np.empty(n, np.int32), np.empty(n + 1, np.int64), np.empty(got[3].size + 8, np.int32))
+    status, total = P.lr_query_all_host(ctx.handle, None, w.rank, w.lcp, *h)
+    assert status == P.LR_OK
+    _assert_csr_equal((h[0], h[1], h[2], h[3][:total]), got, "host buffers, rank windows")
 
 
 def test_maximum_size_closed_form(ctx):
