@@ -361,6 +361,35 @@ __device__ __forceinline__ void part_reserve_r(const PartSmem& p, int nb, unsign
     }
 }
 
+// The same by warp 0 alone, for at most kWarp * R buckets (R consecutive
+// buckets per lane); the other warps wait at the caller's next barrier.
+// Each lane writes the staging offsets of its own buckets in place of their
+// counts after reading them.
+template <int R>
+__device__ __forceinline__ void part_reserve_w(const PartSmem& p, int nb, unsigned* cursor) {
+    if (threadIdx.x >= kWarp) return;
+    const int lane = threadIdx.x;
+    uint32_t a[R], sum = 0;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * lane + u;
+        a[u] = (b < nb) ? p.hist[b] : 0u;
+        sum += a[u];
+    }
+    const int incl = warp_incl_scan((int)sum);
+    uint32_t ex = (uint32_t)incl - sum;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * lane + u;
+        if (b < nb) {
+            p.loff[b] = ex;
+            if (a[u]) p.base[b] = atomicAdd(cursor + (size_t)b * kCursorStride, a[u]);
+        }
+        ex += a[u];
+    }
+    if (lane == kWarp - 1) p.loff[nb] = (uint32_t)incl;
+}
+
 // up to 2048 super-buckets (n <= 2^31 positions in super-buckets of 2^20)
 __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned* cursor) {
     static_assert(4 * kPartThreads >= 2048, "partition CTAs too small for 2048 super-buckets");
@@ -820,7 +849,7 @@ k_part2(int32_t n, Scratch s) {
     __syncthreads();
     const long long bb = b1 * kSubPerSuper;
     const int nsub = (int)((s.nbuckets - bb < kSubPerSuper) ? s.nbuckets - bb : kSubPerSuper);
-    part_reserve(P, nsub, s.cursor2 + (size_t)bb * kCursorStride);
+    part_reserve_w<1>(P, nsub, s.cursor2 + (size_t)bb * kCursorStride);
     __syncthreads();
     unsigned bad = 0;
 #pragma unroll
