@@ -390,6 +390,31 @@ __device__ __forceinline__ void part_reserve_w(const PartSmem& p, int nb, unsign
     if (lane == kWarp - 1) p.loff[nb] = (uint32_t)incl;
 }
 
+// The exclusive scan of hist[0..nb) into loff[0..nb] alone, by warp 0, for
+// at most kWarp * R buckets: k_part1 then reserves each bucket's room with
+// one thread per bucket, in the same phase as its staging writes.
+template <int R>
+__device__ __forceinline__ void part_scan_w(const PartSmem& p, int nb) {
+    if (threadIdx.x >= kWarp) return;
+    const int lane = threadIdx.x;
+    uint32_t a[R], sum = 0;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * lane + u;
+        a[u] = (b < nb) ? p.hist[b] : 0u;
+        sum += a[u];
+    }
+    const int incl = warp_incl_scan((int)sum);
+    uint32_t ex = (uint32_t)incl - sum;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int b = R * lane + u;
+        if (b < nb) p.loff[b] = ex;
+        ex += a[u];
+    }
+    if (lane == kWarp - 1) p.loff[nb] = (uint32_t)incl;
+}
+
 // up to 2048 super-buckets (n <= 2^31 positions in super-buckets of 2^20)
 __device__ __forceinline__ void part_reserve(const PartSmem& p, int nb, unsigned* cursor) {
     static_assert(4 * kPartThreads >= 2048, "partition CTAs too small for 2048 super-buckets");
@@ -646,8 +671,16 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
         key[j] = (b1 << 16) | atomicAdd(&P.hist[b1], 1u);
     }
     __syncthreads();
-    part_reserve(P, nb, s.cursor1);
+    const bool wscan = nb <= 8 * kWarp;
+    if (wscan) part_scan_w<8>(P, nb);
+    else part_reserve(P, nb, s.cursor1);
     __syncthreads();
+    if (wscan) {
+        for (int b = threadIdx.x; b < nb; b += kPartThreads) {
+            const uint32_t c = P.loff[b + 1] - P.loff[b];
+            if (c) P.base[b] = atomicAdd(s.cursor1 + (size_t)b * kCursorStride, c);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         if (key[j] == 0xffffffffu) continue;
