@@ -479,8 +479,16 @@ __device__ __forceinline__ unsigned level1_scatter(const PartSmem& P, int nb, co
         key[j] = ok ? ((b1 << 16) | slot) : 0xffffffffu;
     }
     __syncthreads();
-    part_reserve(P, nb, s.cursor1);
+    const bool wscan = nb <= 8 * kWarp;
+    if (wscan) part_scan_w<8>(P, nb);
+    else part_reserve(P, nb, s.cursor1);
     __syncthreads();
+    if (wscan) {
+        for (int b = threadIdx.x; b < nb; b += kPartThreads) {
+            const uint32_t c = P.loff[b + 1] - P.loff[b];
+            if (c) P.base[b] = atomicAdd(s.cursor1 + (size_t)b * kCursorStride, c);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
         if (key[j] == 0xffffffffu) continue;
@@ -756,7 +764,8 @@ k_rank_win(const int32_t* __restrict__ rank, int32_t n, Scratch s, int tma) {
         key[j] = (w << 16) | atomicAdd(&P.hist[w], 1u);
     }
     __syncthreads();
-    part_reserve(P, nw, s.cursor_w);
+    if (nw <= 2 * kWarp) part_reserve_w<2>(P, nw, s.cursor_w);
+    else part_reserve(P, nw, s.cursor_w);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kPartPer; ++j) {
