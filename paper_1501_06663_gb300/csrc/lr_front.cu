@@ -660,7 +660,8 @@ k_part1(const int32_t* __restrict__ sa, const int32_t* __restrict__ lcp, int32_t
             p[j] = 0xffffffffu; L[j] = 0;
         }
     }
-    // the steps of level1_scatter, kept inline here (as a call they cost this
+    // the steps of level1_scatter, with one shared atomic per entry (pairs in
+    // rank order come in no runs), kept inline here (as a call they cost this
     // kernel 3 %: more register spills)
     uint32_t ent[kPartPer], key[kPartPer];          // key: bucket << 16 | slot, or ~0u
 #pragma unroll
