@@ -258,6 +258,52 @@ def test_513_super_buckets(ctx):
     _assert_csr_equal(_gpu_all(ctx, sa, rank, lcp, "rank"), got, "n = 2^29 + 12345, rank windows")
 
 
+
+def test_maximum_size_batch_closed_form(ctx):
+    """A batch of three strings a^m whose total is 2^31 - 2, the largest the
+    ABI takes, with string boundaries inside partition rounds (the batched
+    rank-order front end then copies lcp slices from unaligned starts and
+    has 2048 super-buckets).  String j of length m at offset o: every length
+    is m - 1 (all beyond the partition entries' length fields and the
+    cover's staged key range), LR_k = {o} at k = 0, {o, o + 1} inside and
+    {o + 1} at k = m - 1; the total exceeds 2^32."""
+    total = 2**31 - 2
+    ms = [(1 << 30) + 4099, (1 << 29) + 3]
+    ms.append(total - sum(ms))
+    free, _ = torch.cuda.mem_get_info()
+    need = total * (4 + 4 + 4 + 4 + 8 + 8 + 16 + 8) + (1 << 30)
+    if free < need:
+        pytest.skip("needs %.0f GB free" % (need / 1e9))
+    off = np.zeros(len(ms) + 1, np.int64)
+    np.cumsum(ms, out=off[1:])
+    sa = torch.empty(total, dtype=torch.int32, device="cuda")
+    lcp = torch.empty(total + len(ms), dtype=torch.int32, device="cuda")
+    for j, m in enumerate(ms):
+        o = int(off[j])
+        sa[o:o + m] = torch.arange(m - 1, -1, -1, dtype=torch.int32, device="cuda")
+        lcp[o + j:o + j + m + 1] = torch.arange(0, m + 1, dtype=torch.int32, device="cuda")
+        lcp[o + j + m] = 0
+    ln, st, offs, starts = ctx.query_batch(_dev(off), lcp, sa=sa, capacity=2 * total)
+    del sa, lcp
+    assert int(offs[total]) == sum(2 * m - 2 for m in ms) == starts.numel()
+    step = 1 << 28
+    base = 0
+    for j, m in enumerate(ms):
+        o = int(off[j])
+        assert bool((ln[o:o + m] == m - 1).all()), j
+        assert bool((st[o:o + m - 1] == o).all()) and int(st[o + m - 1]) == o + 1, j
+        for a in range(0, m, step):                    # offsets: base + (0, 1, 3, 5, ..., 2m - 3)
+            k = torch.arange(a, min(a + step, m), dtype=torch.int64, device="cuda")
+            want = base + torch.where(k == 0, 0, 2 * k - 1)
+            assert bool((offs[o + a:o + a + k.numel()] == want).all()), j
+        del k, want
+        sj = starts[base:base + 2 * m - 2]
+        assert int(sj[0]) == o and int(sj[-1]) == o + 1, j
+        pair = torch.tensor([o, o + 1], dtype=torch.int32, device="cuda")
+        assert bool((sj[1:-1].view(-1, 2) == pair).all()), j
+        base += 2 * m - 2
+
+
 # ------------------------------------------------------------------ API behaviour
 
 def test_capacity_error_keeps_offsets(ctx):
