@@ -408,8 +408,11 @@ def test_bad_rank_in_the_rank_window_front(ctx):
     _assert_csr_equal((h[0], h[1], h[2], h[3][:total]), got, "host buffers, rank windows")
 
 
-def test_maximum_size_closed_form(ctx):
-    """S = a^n with n = 2^31 - 2, the largest n the ABI takes.
+@pytest.mark.parametrize("front", FRONTS)
+def test_maximum_size_closed_form(ctx, front):
+    """S = a^n with n = 2^31 - 2, the largest n the ABI takes, through the
+    rank-order front end and through rank alone (the rank-window front end,
+    512 windows of 2^22 ranks, the last of them partial).
 
     sa[r] = n-1-r, rank[i] = n-1-i, lcp = [0, 1, ..., n-1, 0]; so L_0 = n-1
     and L_i = n-i (all beyond the 16-bit length field of the partition
@@ -425,7 +428,7 @@ def test_maximum_size_closed_form(ctx):
     sa = torch.arange(n - 1, -1, -1, dtype=torch.int32, device="cuda")     # rank is the same array
     lcp = torch.arange(0, n + 1, dtype=torch.int32, device="cuda")
     lcp[n] = 0
-    ln, st, off, starts = ctx.query_all(lcp, sa=sa, capacity=2 * n)
+    ln, st, off, starts = ctx.query_all(lcp, capacity=2 * n, **({"sa": sa} if front == "sa" else {"rank": sa}))
     del sa, lcp
     assert int(off[n]) == 2 * n - 2
     assert bool((ln == n - 1).all())
